@@ -1,0 +1,162 @@
+"""Pins of the oracle's operator-state products against dense Kronecker-built matrices."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from oracle import dense
+import workloads as w
+
+
+def _restrict(Hs, cfg):
+    idx = cfg.astype(np.int64)
+    return Hs[idx][:, idx]
+
+
+def test_apply_matches_dense_12_qubits(mol12, mol12_dense):
+    """(3a,3b) sector of the 12-qubit molecule: source-form apply == dense 4096x4096 H restricted."""
+    _, _, H = mol12
+    s = oracle.Sector.molecular(6, 3, 3)
+    psi = w.random_state(s.dim, w.MOL12.psi_seed)
+    ref = _restrict(mol12_dense, s.configs()) @ psi
+    out = oracle.apply(s, H, psi)
+    assert np.linalg.norm(out - ref) <= 1e-13 * np.linalg.norm(ref)
+    # the full 2^12 space too
+    full = oracle.Sector.full(12)
+    psi_f = w.random_state(4096, 5)
+    out_f = oracle.apply(full, H, psi_f)
+    ref_f = mol12_dense @ psi_f
+    assert np.linalg.norm(out_f - ref_f) <= 1e-13 * np.linalg.norm(ref_f)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_apply_general_complex_sum_full_space(seed):
+    """Non-Hermitian complex Pauli sum (letter form with phases) on 8 qubits."""
+    n = 8
+    x, z, gamma, cre, cim = w.random_pauli_terms(n, 60, seed)
+    S = oracle.build_sum(n, x, z, gamma, cre, cim)
+    Hd = dense.pauli_sum_matrix(n, S.x, S.z, S.c)
+    full = oracle.Sector.full(n)
+    psi = w.random_state(1 << n, 40 + seed)
+    assert np.allclose(oracle.apply(full, S, psi), Hd @ psi, rtol=0, atol=1e-13)
+
+
+def test_apply_multiblock_sector_xxz():
+    """Open XXZ chain, 10 sites, Sz = 0 as blocks (k, 5-k) over the split 5|5."""
+    n = 10
+    x, z, cre, cim = w.xxz_terms(n, 1)
+    S = oracle.build_sum(n, x, z, None, cre, cim)
+    Hd = dense.pauli_sum_matrix(n, S.x, S.z, S.c, sparse=True)
+    s = oracle.Sector(n, oracle.BLOCKS, 5, [(k, 5 - k) for k in range(6)])
+    psi = w.random_state(s.dim, 3)
+    ref = _restrict(Hd, s.configs()) @ psi
+    assert np.allclose(oracle.apply(s, S, psi), ref, rtol=0, atol=1e-13)
+    # H conserves Sz: the sector block of H equals H on the embedded vector
+    emb = np.zeros(1 << n, complex)
+    emb[s.configs().astype(np.int64)] = psi
+    assert np.allclose((Hd @ emb)[s.configs().astype(np.int64)], ref, atol=1e-13)
+
+
+def test_apply_rows_equals_apply(mol12):
+    _, _, H = mol12
+    s = oracle.Sector.molecular(6, 3, 3)
+    psi = w.random_state(s.dim, 4)
+    out = oracle.apply(s, H, psi)
+    rows = np.array([0, 1, 7, 199, 200, 398, 399])
+    assert np.allclose(oracle.apply_rows(s, H, psi, rows), out[rows], rtol=0, atol=1e-13)
+
+
+def test_expect_and_hermiticity(mol12, mol12_dense):
+    _, _, H = mol12
+    s = oracle.Sector.molecular(6, 3, 3)
+    Hr = _restrict(mol12_dense, s.configs())
+    psi = w.random_state(s.dim, 6)
+    phi = w.random_state(s.dim, 7)
+    E, n2 = oracle.expect(s, H, psi)
+    assert abs(E - np.vdot(psi, Hr @ psi)) < 1e-12
+    assert abs(E.imag) < 1e-14
+    assert abs(n2 - np.linalg.norm(Hr @ psi) ** 2) < 1e-11
+    lhs = np.vdot(phi, oracle.apply(s, H, psi))
+    rhs = np.conj(np.vdot(psi, oracle.apply(s, H, phi)))
+    assert abs(lhs - rhs) < 1e-12
+
+
+def test_rotate_single_string_closed_form():
+    """exp(-i theta P) = cos(theta) I - i sin(theta) P for a Pauli string P (P^2 = I)."""
+    n = 6
+    # letter string X0 Y2 Z3 with real coefficient 1 (Hermitian)
+    P = oracle.build_sum(n, np.array([0b101], np.uint64), np.array([0b1100], np.uint64), None,
+                         np.array([1.0]), np.array([0.0]))
+    full = oracle.Sector.full(n)
+    psi = w.random_state(1 << n, 8)
+    Pd = dense.pauli_sum_matrix(n, P.x, P.z, P.c)
+    for theta in (0.3, -1.1, math.pi / 2):
+        out = oracle.rotate(full, P, theta, psi)
+        ref = math.cos(theta) * psi - 1j * math.sin(theta) * (Pd @ psi)
+        assert np.allclose(out, ref, rtol=0, atol=1e-14)
+    assert np.allclose(oracle.rotate(full, P, math.pi / 2, psi), -1j * (Pd @ psi), atol=1e-14)
+
+
+def test_rotate_group_matches_expm():
+    """One X-group of a molecular H (8 qubits) and a pair-double generator vs scipy expm."""
+    norb = 4
+    h, g = w.molecular_integrals(norb, 11)
+    H = oracle.jw_hamiltonian(norb, h, g, eps_drop=1e-12)
+    s = oracle.Sector.molecular(norb, 2, 2)
+    cfg = s.configs().astype(np.int64)
+    xs, counts = np.unique(H.x, return_counts=True)
+    gx = xs[np.argmax(counts * (xs != 0))]
+    sel = H.x == gx
+    G = oracle.PauliSum(2 * norb, H.x[sel], H.z[sel], H.c[sel])
+    Gp = oracle.fermion_sum(2 * norb, w.pair_double_generator(norb, 0, 2))
+    for Gs in (G, Gp):
+        assert not oracle.leaks(s, Gs)
+        Gd = dense.pauli_sum_matrix(2 * norb, Gs.x, Gs.z, Gs.c)
+        assert np.allclose(Gd, Gd.conj().T)
+        psi = w.random_state(s.dim, 9)
+        for theta in (0.37, -2.2):
+            U = sla.expm(-1j * theta * Gd)[np.ix_(cfg, cfg)]
+            assert np.allclose(oracle.rotate(s, Gs, theta, psi), U @ psi, rtol=0, atol=1e-13)
+
+
+def test_pair_double_on_hf_is_a_givens_rotation():
+    """exp(theta tau)|HF> = cos(theta)|HF> +- sin(theta)|D> for a pair double p -> q."""
+    norb, na = 4, 2
+    s = oracle.Sector.molecular(norb, na, na)
+    G = oracle.fermion_sum(2 * norb, w.pair_double_generator(norb, 1, 3))
+    hf = oracle.hf_config(norb, na, na)
+    d = hf ^ ((1 << 1) | (1 << 3)) ^ (((1 << 1) | (1 << 3)) << norb)
+    psi = np.zeros(s.dim, complex)
+    psi[s.index(hf)[0]] = 1.0
+    theta = 0.61
+    out = oracle.rotate(s, G, theta, psi)
+    i_hf, i_d = s.index(hf)[0], s.index(d)[0]
+    assert abs(out[i_hf] - math.cos(theta)) < 1e-14
+    assert abs(abs(out[i_d]) - math.sin(theta)) < 1e-14 and abs(out[i_d].imag) < 1e-14
+    rest = np.delete(out, [i_hf, i_d])
+    assert np.abs(rest).max() < 1e-15
+
+
+def test_leak_detection():
+    """A single JW string of a pair double leaks out of the (Na, Nb) sector; the whole group does not."""
+    norb = 4
+    s = oracle.Sector.molecular(norb, 2, 2)
+    G = oracle.fermion_sum(2 * norb, w.pair_double_generator(norb, 0, 2))
+    assert not oracle.leaks(s, G)
+    one = oracle.PauliSum(G.n, G.x[:1], G.z[:1], G.c[:1])
+    assert oracle.leaks(s, one)
+
+
+def test_rotate_is_unitary_and_additive(mol12):
+    _, _, H = mol12
+    s = oracle.Sector.molecular(6, 3, 3)
+    xs = np.unique(H.x)
+    sel = H.x == xs[len(xs) // 2]
+    G = oracle.PauliSum(12, H.x[sel], H.z[sel], H.c[sel])
+    psi = w.random_state(s.dim, 10)
+    a = oracle.rotate(s, G, 0.4, oracle.rotate(s, G, 0.3, psi))
+    b = oracle.rotate(s, G, 0.7, psi)
+    assert np.allclose(a, b, atol=1e-13)
+    assert abs(np.linalg.norm(b) - 1.0) < 1e-13
