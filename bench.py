@@ -1,0 +1,346 @@
+"""Benchmark of the Pauli-sum operator-state hot path on one GB300 (replicas across GPUs).
+
+Workload: the 24-qubit synthetic molecule (12 spatial orbitals, generator seed 0,
+Jordan-Wigner, canonical reduction with eps_drop 1e-12: M = 29,737 terms in
+G = 5,479 X-mask groups) applied to a seeded random unit state of the
+(6 alpha, 6 beta) sector, D = 853,776.  One step = one pauli_apply (H psi)
+with complex64 storage and FP32 group sums (the default) or complex128 / FP64.
+
+metric: H|psi> term-amplitude updates per second, U / t, with
+U = sum_k #{t in S : t XOR x_k in S} counted exactly from the canonical masks.
+
+Prints one JSON line (see the end of main()).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as w  # noqa: E402
+
+METRIC = "H|psi> term-amplitude updates/s"
+UNIT = "updates/s"
+L2_BYTES = 126 * 2 ** 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# workload bookkeeping (host side, not timed)
+# ---------------------------------------------------------------------------
+def count_updates(x: np.ndarray, n_lo: int, n_hi: int, k_lo: int, k_hi: int) -> int:
+    """U = sum_k #{t in S : t ^ x_k in S} for a single product block (k_lo, k_hi):
+    flipping the bits of a mask with m bits keeps the popcount of a string iff
+    exactly m/2 of them are set, so a half contributes C(m, m/2) C(bits - m, k - m/2)."""
+    def half_count(m, bits, k):
+        if m % 2:
+            return 0
+        a = m // 2
+        if k - a < 0 or k - a > bits - m:
+            return 0
+        return math.comb(m, a) * math.comb(bits - m, k - a)
+    lomask = (1 << n_lo) - 1
+    total = 0
+    for xv in x.tolist():
+        ml = bin(xv & lomask).count("1")
+        mh = bin(xv >> n_lo).count("1")
+        total += half_count(ml, n_lo, k_lo) * half_count(mh, n_hi, k_hi)
+    return total
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_rate(seconds: float = 10.0, max_rows: int | None = None):
+    """Oracle updates/s from the per-target definition on a bounded sample of rows."""
+    import oracle
+    h, g = w.MOL24.integrals()
+    R = oracle.jw_hamiltonian(12, h, g, eps_drop=1e-12)
+    So = oracle.Sector.molecular(12, 6, 6)
+    psi = w.random_state(So.dim, w.MOL24.psi_seed)
+    U = count_updates(R.x, 12, 12, 6, 6)
+    D = So.dim
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    oracle.apply_rows(So, R, psi, rng.integers(0, D, 64))
+    per_row = (time.perf_counter() - t0) / 64
+    nrows = max(64, int(seconds / per_row))
+    if max_rows:
+        nrows = min(nrows, max_rows)
+    rows = rng.integers(0, D, nrows)
+    t0 = time.perf_counter()
+    oracle.apply_rows(So, R, psi, rows)
+    dt = time.perf_counter() - t0
+    est_apply_s = dt / nrows * D
+    return U / est_apply_s, nrows, dt, est_apply_s
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_rate(seconds=1.0)
+    t_all = time.perf_counter()
+    info = None
+    for _ in range(args.steps):
+        v, nrows, dt, est = oracle_rate(seconds=args.ref_seconds)
+        vals.append(v)
+        info = (nrows, dt, est)
+    wall = time.perf_counter() - t_all
+    value = statistics.median(vals)
+    nrows, dt, est = info
+    sample = (f"{nrows} random target rows of the 24-qubit (6a,6b) apply by the per-target definition "
+              f"(sum_k C_k <t|P_k|psi>), {dt:.1f} s, scaled to one full apply ({est:.0f} s)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "mol24: 24 qubits, 12 orbitals, (6a,6b) sector D=853776",
+                                        "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2606_28952_gb300 as ps
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    tdt = torch.complex64 if args.dtype == "c64" else torch.complex128
+    esize = 8 if args.dtype == "c64" else 16
+    h, g = w.MOL24.integrals()
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    S = ps.Sector.molecular(12, 6, 6)
+    ps.prepare(H, S)
+    x_can, _, _ = H.export()
+    U = count_updates(x_can, 12, 12, 6, 6)
+    psi_np = w.random_state(S.dim, w.MOL24.psi_seed)
+    psi = torch.from_numpy(psi_np).to(dev, tdt)
+    out = torch.empty_like(psi)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ps.apply(H, S, psi, out)
+    torch.cuda.synchronize()
+
+    # device-timed region: inputs resident, L2 flushed between timed steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        ps.apply(H, S, psi, out)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    time.sleep(0.2)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    times_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_step = sum(times_ms) / len(times_ms) / 1e3
+    if dist:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = tt.item()
+    value = world * U / t_step
+
+    # end to end: pinned host psi -> device -> apply -> host, every step
+    host_in = torch.from_numpy(psi_np).to(tdt).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_in = torch.empty_like(psi)
+    for _ in range(max(3, args.warmup)):
+        dev_in.copy_(host_in, non_blocking=True)
+        ps.apply(H, S, dev_in, out)
+        host_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(10, args.steps // 4)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        dev_in.copy_(host_in, non_blocking=True)
+        ps.apply(H, S, dev_in, out)
+        host_out.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3 / e2e_steps
+    bytes_io = S.dim * esize
+
+    # roofline bookkeeping for the apply kernel
+    hbm_peak, peak_kind = measured_peaks()
+    table_bytes = H.m * (8 + 8 + 2 * (4 if args.dtype == "c64" else 8)) + H.n_groups * 16
+    alg_bytes = 2 * S.dim * esize + table_bytes
+    achieved_gbs = alg_bytes / t_step / 1e9
+
+    # side measurements (not the headline): expectation value and the other precision
+    res = torch.empty(4, dtype=torch.float64, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ps.expect(H, S, psi, result=res)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(10):
+        ps.expect(H, S, psi, result=res)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_expect = ev0.elapsed_time(ev1) / 1e3 / 10
+    other = torch.complex128 if tdt == torch.complex64 else torch.complex64
+    psi_o = psi.to(other)
+    out_o = torch.empty_like(psi_o)
+    ps.apply(H, S, psi_o, out_o)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(5):
+        ps.apply(H, S, psi_o, out_o)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_other = ev0.elapsed_time(ev1) / 1e3 / 5
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, nrows, dt, est = oracle_rate(seconds=args.ref_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nrows} random target rows by the per-target definition, {dt:.1f} s, "
+                         f"scaled to one full apply ({est:.0f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64/f32" if args.dtype == "c64" else "c128/f64",
+            "data": "synthetic",
+            "config": {"workload": "mol24: 24 qubits, 12 orbitals, seed 0, (6a,6b) sector D=853776",
+                       "terms": H.m, "groups": H.n_groups, "updates_per_apply": U,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"},
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "traffic": None,
+                         "note": f"compulsory bytes {alg_bytes} per apply; peak {peak_kind}"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * U / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "side": {"expect_ms": t_expect * 1e3, f"apply_{'c128' if tdt == torch.complex64 else 'c64'}_ms": t_other * 1e3,
+                     "step_times_ms_min_max": [min(times_ms), max(times_ms)]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

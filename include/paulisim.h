@@ -1,0 +1,214 @@
+/*
+ * paulisim.h -- C ABI of the GB300 (sm_103a) Pauli-algebra operator-state library.
+ *
+ * The library holds Pauli-sum operators H = sum_j C_j X^{x_j} Z^{z_j} in binary
+ * symplectic form (Sec. 2.2-2.3 of "A High-Performance Pauli-Algebra Framework
+ * for Large-Scale Quantum Simulations"), canonically reduced and grouped by
+ * their X masks (eq. topological_group), and applies them to state vectors
+ * with a target-driven gather (eq. reverse_sum) over spin-resolved product
+ * sectors (eq. sreverse_sum, eq. fcidim).  Every step runs in the library's
+ * own CUDA kernels on one GPU.
+ *
+ * Conventions
+ *   - Qubit k is bit k of a basis configuration b (qubit 0 = least significant
+ *     bit, eq. xp_encoding / zp_encoding), n_qubits <= 64.
+ *   - X^x Z^z |b> = (-1)^popcount(z & b) |b XOR x>.
+ *   - A term's coefficient is stored in XZ form: C = c * i^(gamma + popcount(x & z))
+ *     for a LETTER-form input c (where a qubit with both bits set is the letter
+ *     Y), or C = c * i^gamma for an XZ-form input (Sec. 2.2.2, Lambda = i^chi).
+ *   - Canonical form (Sec. 2.3): unique (x, z) sorted ascending as unsigned
+ *     (x first, then z), each coefficient the left-to-right sum of its input
+ *     entries in input order, terms with re*re + im*im <= eps_drop^2 dropped.
+ *   - A sector is the full 2^n space (index = configuration) or a union of
+ *     product blocks r = (k_lo, k_hi): the low n_lo qubits hold k_lo ones and
+ *     the high n - n_lo qubits hold k_hi ones (for a molecule in blocked spin
+ *     order, alpha = low qubits, beta = high qubits, n_lo = n_orb).  Block
+ *     indices follow the order given; inside block r
+ *         index = off_r + rank(b_hi) * D_lo^r + rank(b_lo),
+ *     rank = colex rank among strings of the same popcount (= ascending
+ *     numeric order), D_lo^r = C(n_lo, k_lo).  The k_hi of the blocks must be
+ *     distinct.
+ *   - State vectors are caller-owned DEVICE arrays of interleaved complex
+ *     numbers: PAULI_C64 = (float re, float im), PAULI_C128 = (double re,
+ *     double im), indexed by sector index, 16-byte aligned (8-byte for C64).
+ *   - Work is enqueued on the caller's CUDA stream (`pauli_stream_t` is a
+ *     cudaStream_t; NULL = legacy default stream).  Calls return once the work
+ *     is enqueued unless stated otherwise.
+ *   - Every call returns PAULI_OK (0) or a negative status; the message of the
+ *     last failure on the calling thread is pauli_last_error().  The library
+ *     never aborts or exits.  Errors detected on the device (a rotation that
+ *     leaves the sector) are recorded in a per-handle status word read by
+ *     pauli_status().
+ *   - Ownership: handles own their device tables and are released by the
+ *     matching *_destroy call.  The library never frees caller memory.
+ */
+#ifndef PAULISIM_H
+#define PAULISIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum pauli_status_code {
+    PAULI_OK = 0,
+    PAULI_EINVAL = -1,          /* bad argument (null pointer, size, alias, range)  */
+    PAULI_ENOMEM = -2,          /* device or host allocation failed                 */
+    PAULI_ECUDA = -3,           /* a CUDA runtime call failed                        */
+    PAULI_ESECTOR = -4,         /* a rotation would take amplitude out of the sector */
+    PAULI_ENOTHERMITIAN = -5,   /* rotation generator is not Hermitian               */
+    PAULI_ETIMEOUT = -6,        /* a bounded device wait gave up                     */
+    PAULI_EUNSUPPORTED = -7     /* valid request outside what this build supports    */
+};
+
+enum pauli_dtype { PAULI_C64 = 0, PAULI_C128 = 1 };
+enum pauli_coeff_form { PAULI_LETTER = 0, PAULI_XZ = 1 };
+enum pauli_sector_kind { PAULI_SECTOR_FULL = 0, PAULI_SECTOR_BLOCKS = 1 };
+
+typedef struct pauli_sum pauli_sum;
+typedef struct pauli_sector pauli_sector;
+typedef void *pauli_stream_t;
+
+/* ------------------------------------------------------------------------- */
+/* library                                                                    */
+/* ------------------------------------------------------------------------- */
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next library call on the same thread. */
+const char *pauli_last_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int pauli_version(void);
+
+/* Device allocator for handle tables and plans (default: cudaMalloc/cudaFree).
+ * alloc_fn(bytes, ctx) returns a device pointer or NULL; free_fn(ptr, ctx).
+ * Passing NULL for both restores the default.  Handles remember the allocator
+ * they were created with. */
+int pauli_set_allocator(void *(*alloc_fn)(size_t bytes, void *ctx),
+                        void (*free_fn)(void *ptr, void *ctx), void *ctx);
+
+/* ------------------------------------------------------------------------- */
+/* Pauli sums (Sec. 2.3: binary symplectic arrays X, Z, C; canonical form)    */
+/* ------------------------------------------------------------------------- */
+
+/* Canonical reduction of m input terms (host arrays): sort by (x, z) with a
+ * stable radix sort, sum duplicates in input order, drop |C| <= eps_drop,
+ * then group by x (eq. topological_group).  gamma may be NULL (all 0);
+ * coeff_form is PAULI_LETTER or PAULI_XZ.  Masks must not have bits at or
+ * above n_qubits (PAULI_EINVAL).  Blocking: returns when the handle is ready. */
+int pauli_sum_build(int n_qubits, int64_t m, const uint64_t *x, const uint64_t *z,
+                    const uint8_t *gamma, const double *c_re, const double *c_im, int coeff_form,
+                    double eps_drop, pauli_sum **out);
+
+/* Jordan-Wigner qubit Hamiltonian of Algorithm 1 for n_orb spatial orbitals
+ * (2 n_orb qubits, blocked spin order: spin orbital p-alpha = qubit p,
+ * p-beta = qubit n_orb + p) from host integrals h[n_orb^2] (row-major h_pq)
+ * and g[n_orb^4] (chemist (pq|rs), row-major):
+ *   H = sum_{s,pq} h_pq a+_{ps} a_{qs}
+ *     + 1/2 sum_{s,t,pqrs} (pq|rs) a+_{ps} a+_{rt} a_{st} a_{qs} + e_nn,
+ * a_P = 1/2 (X_P + i Y_P) Z_{<P}.  Integrals with |v| <= eps_int are skipped,
+ * as are two-body terms with P == R or Q == S (identically zero).  Raw entry
+ * order: the e_nn identity entry (if e_nn != 0), one-body (s, p, q ascending,
+ * 4 entries each), two-body (s, t, p, q, r, s ascending, 16 each), entries of
+ * one term in expansion order with the left factor most significant; then
+ * canonical reduction with eps_drop.  n_orb <= 32.  Blocking. */
+int pauli_jw_molecular(int n_orb, const double *h, const double *g, double e_nn, double eps_int,
+                       double eps_drop, pauli_sum **out);
+
+/* The raw (pre-reduction) entries of pauli_jw_molecular in XZ form, written to
+ * host arrays of *count entries; with x == NULL only *count is set. */
+int pauli_jw_molecular_raw(int n_orb, const double *h, const double *g, double e_nn,
+                           double eps_int, int64_t *count, uint64_t *x, uint64_t *z, double *c_re,
+                           double *c_im);
+
+/* Jordan-Wigner image of a sum of fermionic monomials
+ *   sum_t c_t f_{t,0} f_{t,1} ... f_{t,nf_t - 1},  f = a_P (dagger 0) or a_P^dagger (1),
+ * host arrays: n_factors[n_terms] (each 1..8), modes / daggers with all
+ * factors back to back, c_re / c_im[n_terms].  Raw entries term by term in
+ * expansion order, then canonical reduction.  Blocking. */
+int pauli_jw_fermion(int n_qubits, int n_terms, const int *n_factors, const int *modes,
+                     const int *daggers, const double *c_re, const double *c_im, double eps_drop,
+                     pauli_sum **out);
+
+/* Sizes: qubits, canonical terms M and X-mask groups G. */
+int pauli_sum_info(const pauli_sum *h, int *n_qubits, int64_t *m, int64_t *n_groups);
+
+/* Copy the canonical arrays (XZ-form coefficients) to host arrays of M entries. */
+int pauli_sum_export(const pauli_sum *h, uint64_t *x, uint64_t *z, double *c_re, double *c_im);
+
+/* Copy the X-mask group table to host arrays: group_x[G], group_start[G + 1]
+ * (term offsets into the canonical arrays). */
+int pauli_sum_groups(const pauli_sum *h, uint64_t *group_x, int64_t *group_start);
+
+int pauli_sum_destroy(pauli_sum *h);
+
+/* ------------------------------------------------------------------------- */
+/* sectors (Sec. 2.4 spin-resolved product basis and symmetry blocks)        */
+/* ------------------------------------------------------------------------- */
+
+/* kind FULL: n_qubits <= 40, n_lo (1..min(n,24), 0 = default) only sets how
+ * the kernels tile the index; k_lo / k_hi are ignored.  kind BLOCKS:
+ * 1 <= n_lo < n_qubits, n_lo <= 24, n_qubits - n_lo <= 24, 1..33 blocks with
+ * 0 <= k_lo <= n_lo, 0 <= k_hi <= n - n_lo and distinct k_hi.  Blocking. */
+int pauli_sector_create(int n_qubits, int kind, int n_lo, int n_blocks, const int *k_lo,
+                        const int *k_hi, pauli_sector **out);
+
+int pauli_sector_dim(const pauli_sector *s, int64_t *dim);
+
+/* Rank (configuration -> index, -1 if outside the sector) and unrank (index ->
+ * configuration; out-of-range indices give all-ones) of n entries; device
+ * arrays, enqueued on st.  Ranking uses the binomial table
+ * rank(b) = sum_j C(p_j, j + 1) over the ascending set-bit positions p_j of
+ * each half of b. */
+int pauli_sector_rank(const pauli_sector *s, const uint64_t *configs, int64_t n, int64_t *idx,
+                      pauli_stream_t st);
+int pauli_sector_unrank(const pauli_sector *s, const int64_t *idx, int64_t n, uint64_t *configs,
+                        pauli_stream_t st);
+
+int pauli_sector_destroy(pauli_sector *s);
+
+/* ------------------------------------------------------------------------- */
+/* operator-state products (Sec. 2.4, eq. reverse_sum / sreverse_sum)        */
+/* ------------------------------------------------------------------------- */
+
+/* Build (and cache in H) the apply plan for this sector's split (allocates).
+ * pauli_apply / pauli_expect build it on first use; call this first if the
+ * later calls are to be captured in a CUDA graph.  Blocking. */
+int pauli_prepare(pauli_sum *H, const pauli_sector *s);
+
+/* psi_out = P_S H P_S psi_in (sources outside the sector count as zero):
+ *   (H psi)_t = sum_g psi[t XOR x_g] * sum_{k in g} C_k (-1)^popcount(z_k & (t XOR x_g)),
+ * gathered per target t without atomics.  psi_in and psi_out must not
+ * overlap.  C64 accumulates group sums and amplitudes in FP32, C128 in FP64. */
+int pauli_apply(pauli_sum *H, const pauli_sector *s, const void *psi_in, void *psi_out, int dtype,
+                pauli_stream_t st);
+
+/* result[0..3] (DEVICE, 4 doubles) = { Re <psi|H|psi>, Im <psi|H|psi>, ||H psi||^2, <psi|psi> }
+ * (eq. vqe_energy), reduced in FP64 in a fixed order (deterministic).  If
+ * hpsi_out is not NULL, H psi is also stored there (same dtype). */
+int pauli_expect(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype, double *result,
+                 void *hpsi_out, pauli_stream_t st);
+
+/* psi <- exp(-i theta G) psi in place, for a Hermitian G with ONE X mask x
+ * (a single group; Sec. 2.5 and the Trotter factors exp(theta tau) of
+ * Sec. 3.2 with G = i tau).  G maps each pair {t, t XOR x} onto itself with
+ * (G psi)_t = f_t psi_{t XOR x}, f_{t XOR x} = conj(f_t), so
+ *   psi'_t = cos(theta |f_t|) psi_t - i sin(theta |f_t|) f_t / |f_t| psi_{t XOR x}
+ * (x = 0: psi'_t = exp(-i theta f_t) psi_t).  PAULI_EINVAL if G has more than
+ * one X mask, PAULI_ENOTHERMITIAN if a letter-form coefficient has an
+ * imaginary part above 1e-12 max|C|.  If some t in the sector has
+ * t XOR x outside it with f_t != 0, the device status word of G gets
+ * PAULI_ESECTOR (see pauli_status) and those amplitudes are left unchanged. */
+int pauli_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, int dtype,
+                 pauli_stream_t st);
+
+/* Reads and clears H's device status word; synchronizes st.  *code is
+ * PAULI_OK or the first device-side error recorded since the last read. */
+int pauli_status(pauli_sum *H, pauli_stream_t st, int *code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAULISIM_H */

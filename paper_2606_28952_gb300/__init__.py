@@ -1,0 +1,323 @@
+"""paulisim -- GB300 (sm_103a) Pauli-algebra operator-state library, Python binding.
+
+This module only marshals arguments: every step (Jordan-Wigner expansion,
+canonical reduction, grouping, sector ranking, apply / expect / rotate) runs
+in the CUDA kernels of ``libpaulisim.so`` behind the C ABI of
+``include/paulisim.h``.  PyTorch supplies device memory and streams.  There is
+no CPU fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Iterable, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpaulisim.so")
+
+C64, C128 = 0, 1
+LETTER, XZ = 0, 1
+FULL, BLOCKS = 0, 1
+
+OK, EINVAL, ENOMEM, ECUDA, ESECTOR, ENOTHERMITIAN, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "PAULI_OK", -1: "PAULI_EINVAL", -2: "PAULI_ENOMEM", -3: "PAULI_ECUDA", -4: "PAULI_ESECTOR",
+                -5: "PAULI_ENOTHERMITIAN", -6: "PAULI_ETIMEOUT", -7: "PAULI_EUNSUPPORTED"}
+
+
+class PauliError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_vp, _i64, _i32, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+
+# name -> (restype, argtypes); mirrors include/paulisim.h
+SIGNATURES = {
+    "pauli_last_error": (C.c_char_p, []),
+    "pauli_version": (_i32, []),
+    "pauli_set_allocator": (_i32, [_vp, _vp, _vp]),
+    "pauli_sum_build": (_i32, [_i32, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _dbl, _vp]),
+    "pauli_jw_molecular": (_i32, [_i32, _vp, _vp, _dbl, _dbl, _dbl, _vp]),
+    "pauli_jw_molecular_raw": (_i32, [_i32, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp, _vp, _vp]),
+    "pauli_jw_fermion": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _dbl, _vp]),
+    "pauli_sum_info": (_i32, [_vp, _vp, _vp, _vp]),
+    "pauli_sum_export": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "pauli_sum_groups": (_i32, [_vp, _vp, _vp]),
+    "pauli_sum_destroy": (_i32, [_vp]),
+    "pauli_sector_create": (_i32, [_i32, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "pauli_sector_dim": (_i32, [_vp, _vp]),
+    "pauli_sector_rank": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "pauli_sector_unrank": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "pauli_sector_destroy": (_i32, [_vp]),
+    "pauli_prepare": (_i32, [_vp, _vp]),
+    "pauli_apply": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "pauli_expect": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "pauli_rotate": (_i32, [_vp, _vp, _dbl, _vp, _i32, _vp]),
+    "pauli_status": (_i32, [_vp, _vp, _vp]),
+}
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise PauliError(rc, lib().pauli_last_error().decode())
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.complex128:
+        return C128
+    raise TypeError(f"state vectors must be complex64 or complex128, got {t.dtype}")
+
+
+def _check_state(t, dim: int, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != dim:
+        raise ValueError(f"{name} has {t.numel()} elements, the sector has {dim}")
+
+
+# ---------------------------------------------------------------------------
+# Pauli sums
+# ---------------------------------------------------------------------------
+class PauliSum:
+    """Canonical Pauli sum on the device (opaque handle of the C library)."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+
+    # -- construction -------------------------------------------------------
+    @classmethod
+    def from_terms(cls, n: int, x, z, c_re, c_im=None, gamma=None, form: int = LETTER, eps_drop: float = 0.0):
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        z = np.ascontiguousarray(z, dtype=np.uint64)
+        c_re = np.ascontiguousarray(c_re, dtype=np.float64)
+        c_im = np.zeros_like(c_re) if c_im is None else np.ascontiguousarray(c_im, dtype=np.float64)
+        g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.uint8)
+        out = C.c_void_p()
+        _check(lib().pauli_sum_build(n, len(x), _np_ptr(x), _np_ptr(z), None if g is None else _np_ptr(g),
+                                     _np_ptr(c_re), _np_ptr(c_im), form, eps_drop, C.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def jw_molecular(cls, h, g, e_nn: float = 0.0, eps_int: float = 0.0, eps_drop: float = 0.0):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        norb = h.shape[0]
+        out = C.c_void_p()
+        _check(lib().pauli_jw_molecular(norb, _np_ptr(h), _np_ptr(g), e_nn, eps_int, eps_drop, C.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def jw_fermion(cls, n: int, terms, eps_drop: float = 0.0):
+        """terms = [(coefficient, [(mode, dagger), ...]), ...] (left-to-right products)."""
+        nf = np.array([len(f) for _, f in terms], np.int32)
+        modes = np.array([m for _, f in terms for m, _ in f] or [0], np.int32)
+        dag = np.array([int(d) for _, f in terms for _, d in f] or [0], np.int32)
+        cre = np.array([complex(c).real for c, _ in terms] or [0.0], np.float64)
+        cim = np.array([complex(c).imag for c, _ in terms] or [0.0], np.float64)
+        out = C.c_void_p()
+        _check(lib().pauli_jw_fermion(n, len(terms), _np_ptr(nf), _np_ptr(modes), _np_ptr(dag), _np_ptr(cre),
+                                      _np_ptr(cim), eps_drop, C.byref(out)))
+        return cls(out.value)
+
+    # -- properties ---------------------------------------------------------
+    def info(self):
+        n, m, g = C.c_int(), C.c_int64(), C.c_int64()
+        _check(lib().pauli_sum_info(self._h, C.byref(n), C.byref(m), C.byref(g)))
+        return n.value, m.value, g.value
+
+    @property
+    def n(self) -> int:
+        return self.info()[0]
+
+    @property
+    def m(self) -> int:
+        return self.info()[1]
+
+    @property
+    def n_groups(self) -> int:
+        return self.info()[2]
+
+    def export(self):
+        """Canonical (x, z, C) with XZ-form coefficients, as numpy arrays."""
+        _, m, _ = self.info()
+        x = np.zeros(max(m, 1), np.uint64)
+        z = np.zeros(max(m, 1), np.uint64)
+        re = np.zeros(max(m, 1))
+        im = np.zeros(max(m, 1))
+        _check(lib().pauli_sum_export(self._h, _np_ptr(x), _np_ptr(z), _np_ptr(re), _np_ptr(im)))
+        return x[:m], z[:m], re[:m] + 1j * im[:m]
+
+    def groups(self):
+        _, _, g = self.info()
+        gx = np.zeros(max(g, 1), np.uint64)
+        gs = np.zeros(g + 1, np.int64)
+        _check(lib().pauli_sum_groups(self._h, _np_ptr(gx), _np_ptr(gs)))
+        return gx[:g], gs
+
+    def status(self, stream=None) -> int:
+        code = C.c_int()
+        _check(lib().pauli_status(self._h, _stream_ptr(stream), C.byref(code)))
+        return code.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            if _lib is not None:
+                lib().pauli_sum_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def jw_molecular_raw(h, g, e_nn: float = 0.0, eps_int: float = 0.0):
+    """Raw (pre-reduction) Jordan-Wigner entries (x, z, C) as numpy arrays."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    norb = h.shape[0]
+    cnt = C.c_int64(0)
+    _check(lib().pauli_jw_molecular_raw(norb, _np_ptr(h), _np_ptr(g), e_nn, eps_int, C.byref(cnt), None, None,
+                                        None, None))
+    n = cnt.value
+    x = np.zeros(max(n, 1), np.uint64)
+    z = np.zeros(max(n, 1), np.uint64)
+    re = np.zeros(max(n, 1))
+    im = np.zeros(max(n, 1))
+    _check(lib().pauli_jw_molecular_raw(norb, _np_ptr(h), _np_ptr(g), e_nn, eps_int, C.byref(cnt), _np_ptr(x),
+                                        _np_ptr(z), _np_ptr(re), _np_ptr(im)))
+    return x[:n], z[:n], re[:n] + 1j * im[:n]
+
+
+# ---------------------------------------------------------------------------
+# sectors
+# ---------------------------------------------------------------------------
+class Sector:
+    def __init__(self, n: int, kind: int = FULL, n_lo: int = 0, blocks: Sequence = ()):
+        blocks = [tuple(b) for b in blocks]
+        klo = np.array([b[0] for b in blocks] or [0], np.int32)
+        khi = np.array([b[1] for b in blocks] or [0], np.int32)
+        out = C.c_void_p()
+        _check(lib().pauli_sector_create(n, kind, n_lo, len(blocks), _np_ptr(klo), _np_ptr(khi), C.byref(out)))
+        self._h = out
+        self.n, self.kind, self.n_lo, self.blocks = n, kind, n_lo, blocks
+        d = C.c_int64()
+        _check(lib().pauli_sector_dim(self._h, C.byref(d)))
+        self.dim = d.value
+
+    @classmethod
+    def full(cls, n: int, n_lo: int = 0):
+        return cls(n, FULL, n_lo)
+
+    @classmethod
+    def molecular(cls, norb: int, na: int, nb: int):
+        return cls(2 * norb, BLOCKS, norb, [(na, nb)])
+
+    def rank(self, configs, stream=None):
+        """configs: CUDA int64 tensor of bit patterns -> int64 indices (-1 outside)."""
+        import torch
+        configs = configs.contiguous()
+        idx = torch.empty(configs.shape, dtype=torch.int64, device=configs.device)
+        _check(lib().pauli_sector_rank(self._h, C.c_void_p(configs.data_ptr()), configs.numel(),
+                                       C.c_void_p(idx.data_ptr()), _stream_ptr(stream)))
+        return idx
+
+    def unrank(self, idx, stream=None):
+        import torch
+        idx = idx.contiguous()
+        cfg = torch.empty(idx.shape, dtype=torch.int64, device=idx.device)
+        _check(lib().pauli_sector_unrank(self._h, C.c_void_p(idx.data_ptr()), idx.numel(),
+                                         C.c_void_p(cfg.data_ptr()), _stream_ptr(stream)))
+        return cfg
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            if _lib is not None:
+                lib().pauli_sector_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# operator-state products
+# ---------------------------------------------------------------------------
+def prepare(H: PauliSum, s: Sector):
+    _check(lib().pauli_prepare(H._h, s._h))
+
+
+def apply(H: PauliSum, s: Sector, psi_in, psi_out=None, stream=None):
+    """psi_out = P_S H P_S psi_in on the device; returns psi_out."""
+    import torch
+    _check_state(psi_in, s.dim, "psi_in")
+    if psi_out is None:
+        psi_out = torch.empty_like(psi_in)
+    _check_state(psi_out, s.dim, "psi_out")
+    if psi_out.dtype != psi_in.dtype:
+        raise TypeError("psi_in and psi_out must have the same dtype")
+    _check(lib().pauli_apply(H._h, s._h, C.c_void_p(psi_in.data_ptr()), C.c_void_p(psi_out.data_ptr()),
+                             _dtype_code(psi_in), _stream_ptr(stream)))
+    return psi_out
+
+
+def expect(H: PauliSum, s: Sector, psi, hpsi_out=None, result=None, stream=None):
+    """Device tensor [Re E, Im E, ||H psi||^2, <psi|psi>] (float64); optionally stores H psi."""
+    import torch
+    _check_state(psi, s.dim, "psi")
+    if result is None:
+        result = torch.empty(4, dtype=torch.float64, device=psi.device)
+    hp = None
+    if hpsi_out is not None:
+        _check_state(hpsi_out, s.dim, "hpsi_out")
+        hp = C.c_void_p(hpsi_out.data_ptr())
+    _check(lib().pauli_expect(H._h, s._h, C.c_void_p(psi.data_ptr()), _dtype_code(psi),
+                              C.c_void_p(result.data_ptr()), hp, _stream_ptr(stream)))
+    return result
+
+
+def rotate(G: PauliSum, s: Sector, theta: float, psi, stream=None):
+    """psi <- exp(-i theta G) psi in place (G: one Hermitian X-group)."""
+    _check_state(psi, s.dim, "psi")
+    _check(lib().pauli_rotate(G._h, s._h, float(theta), C.c_void_p(psi.data_ptr()), _dtype_code(psi),
+                              _stream_ptr(stream)))
+    return psi

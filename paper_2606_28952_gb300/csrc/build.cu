@@ -1,0 +1,582 @@
+// build.cu -- Pauli-sum construction on the GPU:
+//   * symplectic-form conversion of input terms (Sec. 2.2.2),
+//   * Jordan-Wigner raw entries straight from bitwise products
+//     (Algorithm 1 with eq. pauli_prod_x / pauli_prod_z / pauli_prod_phase),
+//   * canonical reduction: stable radix sort on (X, Z), in-order duplicate
+//     sums, drop below eps (Sec. 2.3),
+//   * X-mask groups (eq. topological_group) and the per-split apply plan.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ps_internal.cuh"
+
+namespace ps {
+namespace {
+
+__device__ __forceinline__ double2 ipow_mul(double2 c, int k) {
+    switch (k & 3) {
+        case 0: return c;
+        case 1: return make_double2(-c.y, c.x);
+        case 2: return make_double2(-c.x, -c.y);
+        default: return make_double2(c.y, -c.x);
+    }
+}
+
+// C = i^gamma * c * (letter ? i^popcount(x & z) : 1)
+__global__ void k_to_xz(int64_t m, const uint64_t *x, const uint64_t *z, const uint8_t *gamma,
+                        const double *cre, const double *cim, int letter, double2 *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int k = gamma ? (int)gamma[i] : 0;
+    if (letter) k += __popcll(x[i] & z[i]);
+    out[i] = ipow_mul(make_double2(cre[i], cim[i]), k);
+}
+
+// ---------------------------------------------------------------------------
+// Jordan-Wigner.  In XZ form a ladder operator is
+//   a_P^dagger = 1/2 X^{e_P} Z^{below} + 1/2 X^{e_P} Z^{below | e_P}
+//   a_P        = 1/2 X^{e_P} Z^{below} - 1/2 X^{e_P} Z^{below | e_P}
+// (the Y letter -/+ i/2 Y_P carries i^#Y = i into XZ form).  A product of
+// factors multiplies left to right with
+//   (X^a Z^b)(X^c Z^d) = (-1)^popcount(b & c) X^(a^c) Z^(b^d).
+// ---------------------------------------------------------------------------
+struct Factor {
+    int P;
+    int dag;
+};
+
+__device__ __forceinline__ int64_t expand(const Factor *f, int nf, double2 scale, int64_t pos,
+                                          uint64_t *ox, uint64_t *oz, double2 *oc) {
+    const int ne = 1 << nf;
+    for (int e = 0; e < ne; ++e) {
+        uint64_t x = 0, z = 0;
+        int neg = 0;
+        double mag = 1.0;
+        for (int j = 0; j < nf; ++j) {
+            const int sel = (e >> (nf - 1 - j)) & 1;
+            const uint64_t bit = 1ull << f[j].P;
+            const uint64_t fx = bit;
+            const uint64_t fz = (bit - 1ull) | (sel ? bit : 0ull);
+            neg ^= __popcll(z & fx) & 1;  // eq. pauli_prod_phase
+            x ^= fx;
+            z ^= fz;
+            if (sel && !f[j].dag) neg ^= 1;  // -1/2 for the Z-carrying term of a_P
+            mag *= 0.5;
+        }
+        const double s = neg ? -mag : mag;
+        ox[pos] = x;
+        oz[pos] = z;
+        oc[pos] = make_double2(scale.x * s, scale.y * s);
+        ++pos;
+    }
+    return pos;
+}
+
+// slot layout: [e_nn] [one-body: (s*norb + p)*norb + q] [two-body: ((((s*2+t)*norb+p)*norb+q)*norb+r)*norb+u]
+__global__ void k_jw_count(int norb, const double *h, const double *g, double e_nn, double eps,
+                           int64_t nslots, int64_t *cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nslots) return;
+    if (i == 0) {
+        cnt[0] = (e_nn != 0.0) ? 1 : 0;
+        return;
+    }
+    int64_t j = i - 1;
+    const int64_t n1 = 2ll * norb * norb;
+    if (j < n1) {
+        int q = (int)(j % norb);
+        int p = (int)((j / norb) % norb);
+        cnt[i] = (fabs(h[p * norb + q]) > eps) ? 4 : 0;
+        return;
+    }
+    j -= n1;
+    int u = (int)(j % norb); j /= norb;
+    int r = (int)(j % norb); j /= norb;
+    int q = (int)(j % norb); j /= norb;
+    int p = (int)(j % norb); j /= norb;
+    int t = (int)(j % 2); j /= 2;
+    int s = (int)j;
+    int P = s * norb + p, Q = s * norb + q, R = t * norb + r, U = t * norb + u;
+    double v = g[(((int64_t)p * norb + q) * norb + r) * norb + u];
+    cnt[i] = (P != R && Q != U && fabs(v) > eps) ? 16 : 0;
+}
+
+__global__ void k_jw_expand(int norb, const double *h, const double *g, double e_nn,
+                            int64_t nslots, const int64_t *cnt, const int64_t *off, uint64_t *ox,
+                            uint64_t *oz, double2 *oc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nslots || cnt[i] == 0) return;
+    int64_t pos = off[i];
+    if (i == 0) {
+        ox[pos] = 0;
+        oz[pos] = 0;
+        oc[pos] = make_double2(e_nn, 0.0);
+        return;
+    }
+    int64_t j = i - 1;
+    const int64_t n1 = 2ll * norb * norb;
+    Factor f[4];
+    if (j < n1) {
+        int q = (int)(j % norb);
+        int p = (int)((j / norb) % norb);
+        int s = (int)(j / ((int64_t)norb * norb));
+        f[0] = {s * norb + p, 1};
+        f[1] = {s * norb + q, 0};
+        expand(f, 2, make_double2(h[p * norb + q], 0.0), pos, ox, oz, oc);
+        return;
+    }
+    j -= n1;
+    int u = (int)(j % norb); j /= norb;
+    int r = (int)(j % norb); j /= norb;
+    int q = (int)(j % norb); j /= norb;
+    int p = (int)(j % norb); j /= norb;
+    int t = (int)(j % 2); j /= 2;
+    int s = (int)j;
+    double v = g[(((int64_t)p * norb + q) * norb + r) * norb + u];
+    f[0] = {s * norb + p, 1};
+    f[1] = {t * norb + r, 1};
+    f[2] = {t * norb + u, 0};
+    f[3] = {s * norb + q, 0};
+    expand(f, 4, make_double2(0.5 * v, 0.0), pos, ox, oz, oc);
+}
+
+__global__ void k_fermion_expand(int nterms, const int *nf, const int *fstart, const int *modes,
+                                 const int *dag, const double *cre, const double *cim,
+                                 const int64_t *off, uint64_t *ox, uint64_t *oz, double2 *oc) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nterms) return;
+    Factor f[8];
+    for (int j = 0; j < nf[t]; ++j) f[j] = {modes[fstart[t] + j], dag[fstart[t] + j]};
+    expand(f, nf[t], make_double2(cre[t], cim[t]), off[t], ox, oz, oc);
+}
+
+// ---------------------------------------------------------------------------
+// canonical reduction
+// ---------------------------------------------------------------------------
+__global__ void k_head_flags(const uint64_t *a, const uint64_t *b, int64_t n, int64_t *flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flag[i] = (i == 0 || a[i] != a[i - 1] || (b && b[i] != b[i - 1])) ? 1 : 0;
+}
+
+__global__ void k_run_starts(const int64_t *flag, const int64_t *id, int64_t n, int64_t *start) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flag[i]) start[id[i]] = i;
+}
+
+// one thread per run: left-to-right sum in stable (input) order, then the drop test
+__global__ void k_run_sums(int64_t nruns, int64_t n, const int64_t *start, const int64_t *perm,
+                           const double2 *c, double eps2, double2 *sum, int64_t *keep) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nruns) return;
+    int64_t a = start[r], b = (r + 1 < nruns) ? start[r + 1] : n;
+    double2 s = c[perm[a]];
+    for (int64_t j = a + 1; j < b; ++j) {
+        double2 v = c[perm[j]];
+        s.x = __dadd_rn(s.x, v.x);
+        s.y = __dadd_rn(s.y, v.y);
+    }
+    sum[r] = s;
+    double mag2 = __dadd_rn(__dmul_rn(s.x, s.x), __dmul_rn(s.y, s.y));
+    keep[r] = (mag2 > eps2) ? 1 : 0;
+}
+
+__global__ void k_compact(int64_t nruns, const int64_t *start, const int64_t *keep,
+                          const int64_t *pos, const uint64_t *kx, const uint64_t *kz,
+                          const double2 *sum, uint64_t *ox, uint64_t *oz, double2 *oc) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nruns || !keep[r]) return;
+    int64_t o = pos[r];
+    ox[o] = kx[start[r]];
+    oz[o] = kz[start[r]];
+    oc[o] = sum[r];
+}
+
+// properties of the reduced sum: any imaginary part, the largest |C|, and the
+// largest imaginary part of a letter-form coefficient c = C i^-popcount(x&z)
+__global__ void k_props(int64_t m, const uint64_t *x, const uint64_t *z, const double2 *c,
+                        unsigned long long *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double2 v = c[i];
+    if (v.y != 0.0) atomicOr(&out[0], 1ull);
+    double mag = sqrt(v.x * v.x + v.y * v.y);
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(mag));
+    int k = __popcll(x[i] & z[i]) & 1;
+    double im_letter = fabs(k ? v.x : v.y);
+    atomicMax(&out[2], (unsigned long long)__double_as_longlong(im_letter));
+}
+
+// ---------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------
+__global__ void k_fill_group_id(int64_t G, const int64_t *gstart, int64_t *gid) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    for (int64_t t = gstart[g]; t < gstart[g + 1]; ++t) gid[t] = g;
+}
+
+// sort key of a term inside the plan: (group id, z_lo, z_hi)
+__global__ void k_plan_keys(int64_t m, int n_lo, int n_hi, const int64_t *gid, const uint64_t *z,
+                            uint64_t *khi, uint64_t *klo) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint64_t lomask = (n_lo >= 64) ? ~0ull : ((1ull << n_lo) - 1ull);
+    uint64_t zlo = z[i] & lomask;
+    uint64_t zhi = z[i] >> n_lo;
+    khi[i] = (uint64_t)gid[i];
+    klo[i] = (zlo << n_hi) | zhi;
+}
+
+__global__ void k_plan_terms(int64_t m, int n_hi, const uint64_t *klo, const int64_t *perm,
+                             const double2 *c, uint32_t *t_zhi, double2 *t_c64, float2 *t_c32) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint64_t hmask = (n_hi >= 64) ? ~0ull : ((1ull << n_hi) - 1ull);
+    t_zhi[i] = (uint32_t)(klo[i] & hmask);
+    double2 v = c[perm[i]];
+    t_c64[i] = v;
+    t_c32[i] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void k_plan_segments(int64_t m, int n_hi, const int64_t *head, const int64_t *sid,
+                                const uint64_t *khi, const uint64_t *klo, int32_t *s_t0,
+                                uint32_t *s_zlo, int64_t *seg_group) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || !head[i]) return;
+    int64_t s = sid[i];
+    s_t0[s] = (int32_t)i;
+    s_zlo[s] = (uint32_t)(klo[i] >> n_hi);
+    seg_group[s] = (int64_t)khi[i];
+}
+
+__global__ void k_plan_group_segs(int64_t S, const int64_t *seg_group, int32_t *g_s0) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    if (s == 0 || seg_group[s] != seg_group[s - 1]) g_s0[seg_group[s]] = (int32_t)s;
+}
+
+__global__ void k_plan_groups(int64_t G, int n_lo, const uint64_t *gx, uint32_t *g_xlo,
+                              uint32_t *g_xhi) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    uint64_t lomask = (n_lo >= 64) ? ~0ull : ((1ull << n_lo) - 1ull);
+    g_xlo[g] = (uint32_t)(gx[g] & lomask);
+    g_xhi[g] = (uint32_t)(gx[g] >> n_lo);
+}
+
+__global__ void k_shift_right(int64_t m, const uint64_t *in, int sh, uint64_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = (sh >= 64) ? 0ull : (in[i] >> sh);
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T>
+T *alloc_copy_d2d(const Allocator &al, const T *src, int64_t n, cudaStream_t st) {
+    T *p = static_cast<T *>(dev_alloc(al, (n > 0 ? n : 1) * sizeof(T)));
+    if (n > 0) PS_CUDA(cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    return p;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+void canonicalize(pauli_sum *h, int64_t m, uint64_t *d_x, uint64_t *d_z, double2 *d_c,
+                  double eps_drop, cudaStream_t st) {
+    const Allocator &al = h->al;
+    h->m = 0;
+    h->G = 0;
+    if (m > 0) {
+        DevBuf<uint64_t> kx(al, m), kz(al, m);
+        DevBuf<int64_t> perm(al, m), flag(al, m), id(al, m);
+        PS_CUDA(cudaMemcpyAsync(kx.p, d_x, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+        PS_CUDA(cudaMemcpyAsync(kz.p, d_z, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+        radix_sort_keys(kx.p, kz.p, perm.p, m, h->n, h->n, al, st);
+        k_head_flags<<<nblk(m), 256, 0, st>>>(kx.p, kz.p, m, flag.p);
+        PS_LAUNCH_CHECK();
+        exclusive_scan_i64(flag.p, id.p, m, al, st);
+        int64_t last_id = 0, last_flag = 0;
+        PS_CUDA(cudaMemcpyAsync(&last_id, id.p + m - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(&last_flag, flag.p + m - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        const int64_t nruns = last_id + last_flag;
+        DevBuf<int64_t> start(al, nruns), keep(al, nruns), pos(al, nruns);
+        DevBuf<double2> sum(al, nruns);
+        k_run_starts<<<nblk(m), 256, 0, st>>>(flag.p, id.p, m, start.p);
+        PS_LAUNCH_CHECK();
+        k_run_sums<<<nblk(nruns), 256, 0, st>>>(nruns, m, start.p, perm.p, d_c, eps_drop * eps_drop,
+                                               sum.p, keep.p);
+        PS_LAUNCH_CHECK();
+        exclusive_scan_i64(keep.p, pos.p, nruns, al, st);
+        int64_t lp = 0, lk = 0;
+        PS_CUDA(cudaMemcpyAsync(&lp, pos.p + nruns - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(&lk, keep.p + nruns - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        const int64_t M = lp + lk;
+        h->m = M;
+        h->x = static_cast<uint64_t *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(uint64_t)));
+        h->z = static_cast<uint64_t *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(uint64_t)));
+        h->c = static_cast<double2 *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(double2)));
+        k_compact<<<nblk(nruns), 256, 0, st>>>(nruns, start.p, keep.p, pos.p, kx.p, kz.p, sum.p,
+                                              h->x, h->z, h->c);
+        PS_LAUNCH_CHECK();
+        PS_CUDA(cudaStreamSynchronize(st));
+    }
+    if (!h->x) {
+        h->x = static_cast<uint64_t *>(dev_alloc(al, sizeof(uint64_t)));
+        h->z = static_cast<uint64_t *>(dev_alloc(al, sizeof(uint64_t)));
+        h->c = static_cast<double2 *>(dev_alloc(al, sizeof(double2)));
+    }
+    // X-mask groups
+    const int64_t M = h->m;
+    if (M > 0) {
+        DevBuf<int64_t> flag(al, M), id(al, M);
+        k_head_flags<<<nblk(M), 256, 0, st>>>(h->x, nullptr, M, flag.p);
+        PS_LAUNCH_CHECK();
+        exclusive_scan_i64(flag.p, id.p, M, al, st);
+        int64_t li = 0, lf = 0;
+        PS_CUDA(cudaMemcpyAsync(&li, id.p + M - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(&lf, flag.p + M - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        const int64_t G = li + lf;
+        h->G = G;
+        h->gstart = static_cast<int64_t *>(dev_alloc(al, (G + 1) * sizeof(int64_t)));
+        h->gx = static_cast<uint64_t *>(dev_alloc(al, G * sizeof(uint64_t)));
+        k_run_starts<<<nblk(M), 256, 0, st>>>(flag.p, id.p, M, h->gstart);
+        PS_LAUNCH_CHECK();
+        PS_CUDA(cudaMemcpyAsync(h->gstart + G, &M, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        // group x = x of its first term
+        std::vector<int64_t> gs(G + 1);
+        PS_CUDA(cudaMemcpyAsync(gs.data(), h->gstart, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        std::vector<uint64_t> hx(M);
+        PS_CUDA(cudaMemcpy(hx.data(), h->x, M * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        std::vector<uint64_t> gx(G);
+        for (int64_t g = 0; g < G; ++g) gx[g] = hx[gs[g]];
+        PS_CUDA(cudaMemcpy(h->gx, gx.data(), G * sizeof(uint64_t), cudaMemcpyHostToDevice));
+        DevBuf<unsigned long long> props(al, 3);
+        PS_CUDA(cudaMemsetAsync(props.p, 0, 3 * sizeof(unsigned long long), st));
+        k_props<<<nblk(M), 256, 0, st>>>(M, h->x, h->z, h->c, props.p);
+        PS_LAUNCH_CHECK();
+        unsigned long long hp[3];
+        PS_CUDA(cudaMemcpyAsync(hp, props.p, sizeof(hp), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        double cmax, imax;
+        memcpy(&cmax, &hp[1], sizeof(double));
+        memcpy(&imax, &hp[2], sizeof(double));
+        h->real = (hp[0] == 0);
+        h->cmax = cmax;
+        h->hermitian = imax <= 1e-12 * cmax;
+    } else {
+        h->gstart = static_cast<int64_t *>(dev_alloc(al, sizeof(int64_t)));
+        h->gx = static_cast<uint64_t *>(dev_alloc(al, sizeof(uint64_t)));
+        PS_CUDA(cudaMemsetAsync(h->gstart, 0, sizeof(int64_t), st));
+        h->real = true;
+        h->hermitian = true;
+        PS_CUDA(cudaStreamSynchronize(st));
+    }
+}
+
+void to_xz_device(int64_t m, const uint64_t *x, const uint64_t *z, const uint8_t *gamma,
+                  const double *cre, const double *cim, int letter, double2 *out, cudaStream_t st) {
+    if (m <= 0) return;
+    k_to_xz<<<nblk(m), 256, 0, st>>>(m, x, z, gamma, cre, cim, letter, out);
+    PS_LAUNCH_CHECK();
+}
+
+void jw_molecular_raw_device(int norb, const double *h, const double *g, double e_nn, double eps_int,
+                             const Allocator &al, DevBuf<uint64_t> &x, DevBuf<uint64_t> &z,
+                             DevBuf<double2> &c, int64_t &count, cudaStream_t st) {
+    const int64_t n1 = 2ll * norb * norb;
+    const int64_t n4 = (int64_t)norb * norb * norb * norb;
+    const int64_t nslots = 1 + n1 + 4 * n4;
+    DevBuf<double> dh(al, (size_t)norb * norb), dg(al, (size_t)n4);
+    PS_CUDA(cudaMemcpyAsync(dh.p, h, norb * norb * sizeof(double), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(dg.p, g, n4 * sizeof(double), cudaMemcpyHostToDevice, st));
+    DevBuf<int64_t> cnt(al, nslots), off(al, nslots);
+    k_jw_count<<<nblk(nslots), 256, 0, st>>>(norb, dh.p, dg.p, e_nn, eps_int, nslots, cnt.p);
+    PS_LAUNCH_CHECK();
+    exclusive_scan_i64(cnt.p, off.p, nslots, al, st);
+    int64_t lo = 0, lc = 0;
+    PS_CUDA(cudaMemcpyAsync(&lo, off.p + nslots - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(&lc, cnt.p + nslots - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    count = lo + lc;
+    x = DevBuf<uint64_t>(al, count);
+    z = DevBuf<uint64_t>(al, count);
+    c = DevBuf<double2>(al, count);
+    k_jw_expand<<<nblk(nslots), 256, 0, st>>>(norb, dh.p, dg.p, e_nn, nslots, cnt.p, off.p, x.p, z.p,
+                                              c.p);
+    PS_LAUNCH_CHECK();
+    PS_CUDA(cudaStreamSynchronize(st));
+}
+
+void jw_fermion_raw_device(int n, int nterms, const int *nf, const int *modes, const int *dag,
+                           const double *cre, const double *cim, const Allocator &al,
+                           DevBuf<uint64_t> &x, DevBuf<uint64_t> &z, DevBuf<double2> &c,
+                           int64_t &count, cudaStream_t st) {
+    (void)n;
+    std::vector<int> fstart(nterms + 1, 0);
+    std::vector<int64_t> off(nterms, 0);
+    count = 0;
+    for (int t = 0; t < nterms; ++t) {
+        fstart[t + 1] = fstart[t] + nf[t];
+        off[t] = count;
+        count += (int64_t)1 << nf[t];
+    }
+    const int nfac = fstart[nterms];
+    DevBuf<int> d_nf(al, nterms), d_fs(al, nterms + 1), d_modes(al, nfac), d_dag(al, nfac);
+    DevBuf<double> d_re(al, nterms), d_im(al, nterms);
+    DevBuf<int64_t> d_off(al, nterms);
+    PS_CUDA(cudaMemcpyAsync(d_nf.p, nf, nterms * sizeof(int), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(d_fs.p, fstart.data(), (nterms + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (nfac > 0) {
+        PS_CUDA(cudaMemcpyAsync(d_modes.p, modes, nfac * sizeof(int), cudaMemcpyHostToDevice, st));
+        PS_CUDA(cudaMemcpyAsync(d_dag.p, dag, nfac * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    PS_CUDA(cudaMemcpyAsync(d_re.p, cre, nterms * sizeof(double), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(d_im.p, cim, nterms * sizeof(double), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(d_off.p, off.data(), nterms * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    x = DevBuf<uint64_t>(al, count);
+    z = DevBuf<uint64_t>(al, count);
+    c = DevBuf<double2>(al, count);
+    k_fermion_expand<<<nblk(nterms), 256, 0, st>>>(nterms, d_nf.p, d_fs.p, d_modes.p, d_dag.p, d_re.p,
+                                                   d_im.p, d_off.p, x.p, z.p, c.p);
+    PS_LAUNCH_CHECK();
+    PS_CUDA(cudaStreamSynchronize(st));
+}
+
+void free_plan(const Allocator &al, Plan &p) {
+    dev_free(al, p.g_xlo); dev_free(al, p.g_xhi); dev_free(al, p.g_s0);
+    dev_free(al, p.s_zlo); dev_free(al, p.s_t0);
+    dev_free(al, p.t_zhi); dev_free(al, p.t_c64); dev_free(al, p.t_c32);
+    dev_free(al, p.b_i0); dev_free(al, p.it_g); dev_free(al, p.it_s0); dev_free(al, p.s_xhi);
+    dev_free(al, p.partials);
+    p = Plan();
+}
+
+Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
+    for (int i = 0; i < h->nplans; ++i)
+        if (h->plans[i].n_lo == n_lo) return h->plans[i];
+    if (h->nplans == 4) {  // evict the oldest
+        free_plan(h->al, h->plans[0]);
+        for (int i = 1; i < 4; ++i) h->plans[i - 1] = h->plans[i];
+        h->plans[3] = Plan();
+        h->nplans = 3;
+    }
+    const Allocator &al = h->al;
+    const int n_hi = h->n - n_lo;
+    const int64_t M = h->m, G = h->G;
+    Plan p;
+    p.n_lo = n_lo;
+    p.M = M;
+    p.G = G;
+    p.real = h->real;
+    p.g_xlo = static_cast<uint32_t *>(dev_alloc(al, (G > 0 ? G : 1) * sizeof(uint32_t)));
+    p.g_xhi = static_cast<uint32_t *>(dev_alloc(al, (G > 0 ? G : 1) * sizeof(uint32_t)));
+    p.g_s0 = static_cast<int32_t *>(dev_alloc(al, (G + 1) * sizeof(int32_t)));
+    p.t_zhi = static_cast<uint32_t *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(uint32_t)));
+    p.t_c64 = static_cast<double2 *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(double2)));
+    p.t_c32 = static_cast<float2 *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(float2)));
+    std::vector<int32_t> hs0(G + 1, 0);
+    int64_t S = 0;
+    if (M > 0) {
+        k_plan_groups<<<nblk(G), 256, 0, st>>>(G, n_lo, h->gx, p.g_xlo, p.g_xhi);
+        PS_LAUNCH_CHECK();
+        DevBuf<int64_t> gid(al, M), perm(al, M), head(al, M), sid(al, M);
+        DevBuf<uint64_t> khi(al, M), klo(al, M);
+        k_fill_group_id<<<nblk(G), 256, 0, st>>>(G, h->gstart, gid.p);
+        PS_LAUNCH_CHECK();
+        k_plan_keys<<<nblk(M), 256, 0, st>>>(M, n_lo, n_hi, gid.p, h->z, khi.p, klo.p);
+        PS_LAUNCH_CHECK();
+        int gbits = 1;
+        while ((1ll << gbits) <= G) ++gbits;
+        radix_sort_keys(khi.p, klo.p, perm.p, M, gbits, h->n, al, st);
+        k_plan_terms<<<nblk(M), 256, 0, st>>>(M, n_hi, klo.p, perm.p, h->c, p.t_zhi, p.t_c64, p.t_c32);
+        PS_LAUNCH_CHECK();
+        // segments: runs of equal (group, z_lo); z_lo = klo >> n_hi
+        DevBuf<uint64_t> seg_key(al, M);
+        k_shift_right<<<nblk(M), 256, 0, st>>>(M, klo.p, n_hi, seg_key.p);
+        PS_LAUNCH_CHECK();
+        k_head_flags<<<nblk(M), 256, 0, st>>>(khi.p, seg_key.p, M, head.p);
+        PS_LAUNCH_CHECK();
+        exclusive_scan_i64(head.p, sid.p, M, al, st);
+        int64_t ls = 0, lh = 0;
+        PS_CUDA(cudaMemcpyAsync(&ls, sid.p + M - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(&lh, head.p + M - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        S = ls + lh;
+        p.s_zlo = static_cast<uint32_t *>(dev_alloc(al, S * sizeof(uint32_t)));
+        p.s_t0 = static_cast<int32_t *>(dev_alloc(al, (S + 1) * sizeof(int32_t)));
+        DevBuf<int64_t> seg_group(al, S);
+        k_plan_segments<<<nblk(M), 256, 0, st>>>(M, n_hi, head.p, sid.p, khi.p, klo.p, p.s_t0, p.s_zlo,
+                                                  seg_group.p);
+        PS_LAUNCH_CHECK();
+        int32_t m32 = (int32_t)M;
+        PS_CUDA(cudaMemcpyAsync(p.s_t0 + S, &m32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        k_plan_group_segs<<<nblk(S), 256, 0, st>>>(S, seg_group.p, p.g_s0);
+        PS_LAUNCH_CHECK();
+        int32_t s32 = (int32_t)S;
+        PS_CUDA(cudaMemcpyAsync(p.g_s0 + G, &s32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        PS_CUDA(cudaMemcpyAsync(hs0.data(), p.g_s0, (G + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+    } else {
+        p.s_zlo = static_cast<uint32_t *>(dev_alloc(al, sizeof(uint32_t)));
+        p.s_t0 = static_cast<int32_t *>(dev_alloc(al, sizeof(int32_t)));
+        PS_CUDA(cudaMemset(p.s_t0, 0, sizeof(int32_t)));
+        PS_CUDA(cudaMemset(p.g_s0, 0, sizeof(int32_t)));
+    }
+    p.S = S;
+    // items: (group, contiguous segment range) of at most kSegsPerBatch segments;
+    // batches: consecutive items with at most kGroupsPerBatch items and
+    // kSegsPerBatch segments in total.
+    std::vector<int32_t> it_g, it_s0, b_i0;
+    b_i0.push_back(0);
+    int items_in_batch = 0, segs_in_batch = 0;
+    for (int64_t g = 0; g < G; ++g) {
+        int32_t s = hs0[g];
+        const int32_t se = hs0[g + 1];
+        while (s < se) {
+            int32_t take = std::min<int32_t>(se - s, PlanLimits::kSegsPerBatch);
+            if (items_in_batch == PlanLimits::kGroupsPerBatch ||
+                segs_in_batch + take > PlanLimits::kSegsPerBatch) {
+                b_i0.push_back((int32_t)it_g.size());
+                items_in_batch = 0;
+                segs_in_batch = 0;
+            }
+            it_g.push_back((int32_t)g);
+            it_s0.push_back(s);
+            ++items_in_batch;
+            segs_in_batch += take;
+            s += take;
+        }
+    }
+    it_s0.push_back((int32_t)S);
+    if (!it_g.empty()) b_i0.push_back((int32_t)it_g.size());
+    p.nbatch = (int64_t)b_i0.size() - 1;
+    p.nitem = (int64_t)it_g.size();
+    p.h_b_i0 = b_i0;
+    p.b_i0 = static_cast<int32_t *>(dev_alloc(al, b_i0.size() * sizeof(int32_t)));
+    p.it_g = static_cast<int32_t *>(dev_alloc(al, (it_g.empty() ? 1 : it_g.size()) * sizeof(int32_t)));
+    p.it_s0 = static_cast<int32_t *>(dev_alloc(al, it_s0.size() * sizeof(int32_t)));
+    PS_CUDA(cudaMemcpy(p.b_i0, b_i0.data(), b_i0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!it_g.empty())
+        PS_CUDA(cudaMemcpy(p.it_g, it_g.data(), it_g.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    PS_CUDA(cudaMemcpy(p.it_s0, it_s0.data(), it_s0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // x_hi of each segment's group (phase 1 of the apply kernel reads it per segment)
+    {
+        std::vector<uint32_t> hxhi(G > 0 ? G : 1), sx(S > 0 ? S : 1);
+        if (G > 0) PS_CUDA(cudaMemcpy(hxhi.data(), p.g_xhi, G * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        for (int64_t g = 0; g < G; ++g)
+            for (int32_t s = hs0[g]; s < hs0[g + 1]; ++s) sx[s] = hxhi[g];
+        p.s_xhi = static_cast<uint32_t *>(dev_alloc(al, (S > 0 ? S : 1) * sizeof(uint32_t)));
+        if (S > 0) PS_CUDA(cudaMemcpy(p.s_xhi, sx.data(), S * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
+    h->plans[h->nplans] = p;
+    return h->plans[h->nplans++];
+}
+
+}  // namespace ps

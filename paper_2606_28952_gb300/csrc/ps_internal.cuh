@@ -1,0 +1,207 @@
+// ps_internal.cuh -- shared internals of the paulisim CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/paulisim.h"
+
+namespace ps {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+void clear_error();
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define PS_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            throw ::ps::Error{PAULI_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define PS_CHECK(cond, code, msg)                          \
+    do {                                                   \
+        if (!(cond)) throw ::ps::Error{(code), (msg)};     \
+    } while (0)
+
+#define PS_LAUNCH_CHECK() PS_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// device memory (allocator hook)
+// ---------------------------------------------------------------------------
+struct Allocator {
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+Allocator current_allocator();
+void set_current_allocator(const Allocator &a);
+
+void *dev_alloc(const Allocator &a, size_t bytes);
+void dev_free(const Allocator &a, void *p);
+
+// RAII device buffer (library-internal temporaries at build time).
+template <typename T>
+struct DevBuf {
+    Allocator al;
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const Allocator &a, size_t count) : al(a), n(count) {
+        p = static_cast<T *>(dev_alloc(al, (count ? count : 1) * sizeof(T)));
+    }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : al(o.al), p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { reset(); al = o.al; p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { reset(); }
+    void reset() { if (p) dev_free(al, p); p = nullptr; n = 0; }
+    T *release() { T *q = p; p = nullptr; n = 0; return q; }
+};
+
+// ---------------------------------------------------------------------------
+// sector
+// ---------------------------------------------------------------------------
+constexpr int kMaxBlocks = 33;
+constexpr int kMaxHalf = 24;  // largest half width with rank / unrank tables
+
+// Everything a kernel needs to know about a sector, passed by value.
+struct SectorView {
+    int n, n_lo, n_hi, kind, nblk;
+    int64_t dim;
+    int64_t nrows;                    // sum over blocks of D_hi
+    int klo[kMaxBlocks], khi[kMaxBlocks];
+    int64_t off[kMaxBlocks + 1];      // first index of each block
+    int64_t dlo[kMaxBlocks], dhi[kMaxBlocks];
+    int64_t row_off[kMaxBlocks + 1];  // first row of each block
+    int blk_of_khi[kMaxHalf + 9];     // k_hi -> block or -1 (size n_hi + 1 used)
+    const uint32_t *rank_lo;          // [2^n_lo] colex rank among equal popcount
+    const uint32_t *rank_hi;          // [2^n_hi]
+    const uint32_t *list_lo;          // [2^n_lo] strings ordered by (popcount, value)
+    const uint32_t *list_hi;          // [2^n_hi]
+    int64_t list_lo_off[kMaxHalf + 2];  // first entry of each popcount in list_lo
+    int64_t list_hi_off[kMaxHalf + 2];
+};
+
+// ---------------------------------------------------------------------------
+// apply plan: the canonical sum re-laid out for one sector split (rows = high
+// n - n_lo qubits, columns = low n_lo qubits)
+// ---------------------------------------------------------------------------
+struct Plan {
+    int n_lo = -1;
+    int64_t G = 0, S = 0, M = 0;      // groups, segments, terms
+    int64_t nbatch = 0;
+    bool real = true;                  // every C_k real
+    // per group (canonical group order, i.e. ascending x)
+    uint32_t *g_xlo = nullptr, *g_xhi = nullptr;
+    int32_t *g_s0 = nullptr;           // [G+1] segment range
+    // per segment: equal z_lo within a group, terms sorted by (z_lo, z_hi)
+    uint32_t *s_zlo = nullptr;
+    int32_t *s_t0 = nullptr;           // [S+1] term range
+    // per term (segment order)
+    uint32_t *t_zhi = nullptr;
+    double2 *t_c64 = nullptr;          // FP64 coefficients
+    float2 *t_c32 = nullptr;           // FP32 coefficients
+    uint32_t *s_xhi = nullptr;         // [S] x_hi of the segment's group
+    // items: (group, contiguous segment range) pieces; batches: consecutive
+    // items whose segments fit the apply kernel's shared memory
+    int64_t nitem = 0;
+    int32_t *it_g = nullptr;           // [nitem] group of each item
+    int32_t *it_s0 = nullptr;          // [nitem+1] segment range of each item
+    int32_t *b_i0 = nullptr;           // [nbatch+1] item range of each batch
+    std::vector<int32_t> h_b_i0;
+    // reduction scratch for pauli_expect
+    double *partials = nullptr;
+    int64_t partials_cap = 0;
+    void *owner_alloc_ctx = nullptr;
+};
+
+struct PlanLimits {
+    static constexpr int kGroupsPerBatch = 128;
+    static constexpr int kSegsPerBatch = 1024;
+};
+
+}  // namespace ps
+
+// ---------------------------------------------------------------------------
+// opaque handles
+// ---------------------------------------------------------------------------
+struct pauli_sum {
+    uint32_t magic;
+    ps::Allocator al;
+    int n;
+    int64_t m = 0, G = 0;
+    bool real = true;        // every C imaginary part == 0
+    bool hermitian = true;   // letter-form coefficients real (within 1e-12 max|C|)
+    double cmax = 0.0;
+    uint64_t *x = nullptr, *z = nullptr;  // [m] canonical
+    double2 *c = nullptr;                 // [m]
+    uint64_t *gx = nullptr;               // [G]
+    int64_t *gstart = nullptr;            // [G+1]
+    int *status = nullptr;                // device status word
+    ps::Plan plans[4];
+    int nplans = 0;
+};
+
+struct pauli_sector {
+    uint32_t magic;
+    ps::Allocator al;
+    ps::SectorView v;
+    uint32_t *tables = nullptr;  // backing store of rank / list tables
+};
+
+namespace ps {
+constexpr uint32_t kSumMagic = 0x50534d31u;     // "PSM1"
+constexpr uint32_t kSectorMagic = 0x50534331u;  // "PSC1"
+
+// build.cu
+void to_xz_device(int64_t m, const uint64_t *x, const uint64_t *z, const uint8_t *gamma,
+                  const double *cre, const double *cim, int letter, double2 *out, cudaStream_t st);
+void canonicalize(pauli_sum *h, int64_t m, uint64_t *d_x, uint64_t *d_z, double2 *d_c,
+                  double eps_drop, cudaStream_t st);
+void jw_molecular_raw_device(int norb, const double *h, const double *g, double e_nn,
+                             double eps_int, const Allocator &al, DevBuf<uint64_t> &x,
+                             DevBuf<uint64_t> &z, DevBuf<double2> &c, int64_t &count,
+                             cudaStream_t st);
+void jw_fermion_raw_device(int n, int nterms, const int *nf, const int *modes, const int *dag,
+                           const double *cre, const double *cim, const Allocator &al,
+                           DevBuf<uint64_t> &x, DevBuf<uint64_t> &z, DevBuf<double2> &c,
+                           int64_t &count, cudaStream_t st);
+Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st);
+void free_plan(const Allocator &al, Plan &p);
+
+// scan.cu
+void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, const Allocator &al,
+                        cudaStream_t st);
+// Stable LSD radix sort of (hi, lo) 128-bit keys over the given significant
+// bit counts; perm receives the original index of each sorted element.
+void radix_sort_keys(uint64_t *hi, uint64_t *lo, int64_t *perm, int64_t n, int hi_bits,
+                     int lo_bits, const Allocator &al, cudaStream_t st);
+
+// sector.cu
+void build_sector_tables(pauli_sector *s, cudaStream_t st);
+void sector_rank(const SectorView &v, const uint64_t *cfg, int64_t n, int64_t *idx, cudaStream_t st);
+void sector_unrank(const SectorView &v, const int64_t *idx, int64_t n, uint64_t *cfg,
+                   cudaStream_t st);
+
+// apply.cu
+void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *psi_in,
+                  void *psi_out, int dtype, double *partials, cudaStream_t st);
+void launch_reduce(const double *partials, int64_t nparts, double *result, cudaStream_t st);
+int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype);
+void launch_rotate(pauli_sum *G, const SectorView &v, double theta, void *psi, int dtype,
+                   cudaStream_t st);
+}  // namespace ps

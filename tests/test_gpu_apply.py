@@ -1,0 +1,282 @@
+"""GPU apply / expect / rotate vs the oracle on the same seeded inputs.
+
+Tolerances (spec contract): ||H psi||-relative error <= 1e-12 for the
+FP64 (complex128) path and <= 1e-5 for the FP32 (complex64) path, the latter
+measured against the oracle run on the complex64-rounded input; energies within
+1e-6 Ha (1e-12 for FP64)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-12, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import torch
+    import paper_2606_28952_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def _tdt(name):
+    import torch
+    return torch.complex128 if name == "c128" else torch.complex64
+
+
+def _to_dev(psi, name):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(psi)).to("cuda", _tdt(name))
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _mol(norb, na, nb, seed=0, eps=1e-12):
+    h, g = w.molecular_integrals(norb, seed)
+    return h, g, oracle.jw_hamiltonian(norb, h, g, eps_drop=eps)
+
+
+# ----------------------------------------------------------------------------
+# apply, whole vectors
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("norb,na,nb", [(6, 3, 3), (8, 4, 4), (7, 2, 5), (10, 5, 5)])
+def test_apply_molecular_sector(ps, dt, norb, na, nb):
+    h, g, R = _mol(norb, na, nb)
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    S = ps.Sector.molecular(norb, na, nb)
+    So = oracle.Sector.molecular(norb, na, nb)
+    psi = w.random_state(S.dim, 100 + norb)
+    x = _to_dev(psi, dt)
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    ref = oracle.apply(So, R, x.cpu().numpy().astype(np.complex128))
+    assert _rel(out, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("n,n_lo", [(8, 0), (12, 5), (13, 10)])
+def test_apply_full_space_complex_sum(ps, dt, n, n_lo):
+    """Non-Hermitian complex Pauli sum (complex-coefficient path), full 2^n space."""
+    x_, z_, gamma, cre, cim = w.random_pauli_terms(n, 300, 5 + n, dup_frac=0.2)
+    H = ps.PauliSum.from_terms(n, x_, z_, cre, cim, gamma=gamma)
+    R = oracle.build_sum(n, x_, z_, gamma, cre, cim)
+    S = ps.Sector.full(n, n_lo)
+    So = oracle.Sector.full(n)
+    psi = w.random_state(1 << n, 9)
+    x = _to_dev(psi, dt)
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    ref = oracle.apply(So, R, x.cpu().numpy().astype(np.complex128))
+    assert _rel(out, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_apply_multiblock_sz0_xxz(ps, dt):
+    """Open XXZ chain, 14 sites, Sz = 0 as 8 product blocks (k, 7-k) of a 7|7 split."""
+    n = 14
+    x_, z_, cre, cim = w.xxz_terms(n, 1)
+    H = ps.PauliSum.from_terms(n, x_, z_, cre, cim)
+    R = oracle.build_sum(n, x_, z_, None, cre, cim)
+    blocks = [(k, 7 - k) for k in range(8)]
+    S = ps.Sector(n, ps.BLOCKS, 7, blocks)
+    So = oracle.Sector(n, oracle.BLOCKS, 7, blocks)
+    psi = w.random_state(S.dim, 21)
+    x = _to_dev(psi, dt)
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    ref = oracle.apply(So, R, x.cpu().numpy().astype(np.complex128))
+    assert _rel(out, ref) <= TOL[dt]
+
+
+def test_apply_edge_cases(ps):
+    import torch
+    # empty operator -> zero vector
+    H0 = ps.PauliSum.from_terms(6, [], [], [])
+    S = ps.Sector.molecular(3, 1, 2)
+    x = _to_dev(w.random_state(S.dim, 1), "c128")
+    assert torch.count_nonzero(ps.apply(H0, S, x)).item() == 0
+    # one-configuration sectors (k = 0 and k = n) and a diagonal-only operator
+    h, g = w.molecular_integrals(4, 3)
+    H = ps.PauliSum.jw_molecular(h, g)
+    R = oracle.jw_hamiltonian(4, h, g)
+    for na, nb in [(0, 0), (4, 4), (0, 4), (1, 0)]:
+        S = ps.Sector.molecular(4, na, nb)
+        So = oracle.Sector.molecular(4, na, nb)
+        psi = w.random_state(S.dim, 2)
+        out = ps.apply(H, S, _to_dev(psi, "c128")).cpu().numpy()
+        assert _rel(out, oracle.apply(So, R, psi)) <= 1e-12
+    # in-place (aliased) apply is rejected
+    S = ps.Sector.molecular(4, 2, 2)
+    y = _to_dev(w.random_state(S.dim, 3), "c128")
+    with pytest.raises(ps.PauliError):
+        ps.apply(H, S, y, y)
+
+
+# ----------------------------------------------------------------------------
+# full-size workload: 24 qubits, (6a,6b), D = 853,776 -- sampled rows + properties
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def mol24(ps):
+    h, g = w.MOL24.integrals()
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    R = oracle.jw_hamiltonian(12, h, g, eps_drop=1e-12)
+    S = ps.Sector.molecular(12, 6, 6)
+    So = oracle.Sector.molecular(12, 6, 6)
+    psi = w.random_state(S.dim, w.MOL24.psi_seed)
+    return h, g, H, R, S, So, psi
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_apply_24_qubits_sampled_rows(ps, mol24, dt):
+    h, g, H, R, S, So, psi = mol24
+    x = _to_dev(psi, dt)
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    xin = x.cpu().numpy().astype(np.complex128)
+    rng = np.random.default_rng(5)
+    D = S.dim
+    rows = np.unique(np.concatenate([rng.integers(0, D, 200), [0, 1, 923, 924, 925, D - 925, D - 2, D - 1]]))
+    ref = oracle.apply_rows(So, R, xin, rows)
+    assert np.linalg.norm(out[rows] - ref) <= TOL[dt] * 1.5 * np.linalg.norm(ref)
+
+
+def test_apply_24_qubits_properties(ps, mol24):
+    """Hermiticity <phi|H psi> = conj <psi|H phi> and c64 vs c128 agreement at full size."""
+    h, g, H, R, S, So, psi = mol24
+    phi = w.random_state(S.dim, 99)
+    a = ps.apply(H, S, _to_dev(psi, "c128")).cpu().numpy()
+    b = ps.apply(H, S, _to_dev(phi, "c128")).cpu().numpy()
+    assert abs(np.vdot(phi, a) - np.conj(np.vdot(psi, b))) <= 1e-12 * np.linalg.norm(a) * np.linalg.norm(b) * 10
+    a32 = ps.apply(H, S, _to_dev(psi, "c64")).cpu().numpy().astype(np.complex128)
+    assert _rel(a32, a) <= 1e-5
+
+
+# ----------------------------------------------------------------------------
+# expectation values
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_expect_matches_oracle_and_hf(ps, dt):
+    h, g, R = _mol(6, 3, 3)
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    S = ps.Sector.molecular(6, 3, 3)
+    So = oracle.Sector.molecular(6, 3, 3)
+    psi = w.random_state(S.dim, 11)
+    x = _to_dev(psi, dt)
+    hp = _to_dev(np.zeros(S.dim, complex), dt)
+    res = ps.expect(H, S, x, hpsi_out=hp).cpu().numpy()
+    xin = x.cpu().numpy().astype(np.complex128)
+    E, n2 = oracle.expect(So, R, xin)
+    assert abs(complex(res[0], res[1]) - E) <= (1e-12 if dt == "c128" else 1e-6)
+    assert abs(res[2] - n2) <= (1e-11 if dt == "c128" else 1e-5) * n2
+    assert abs(res[3] - np.vdot(xin, xin).real) <= 1e-12
+    assert _rel(hp.cpu().numpy().astype(np.complex128), oracle.apply(So, R, xin)) <= TOL[dt]
+    # Hartree-Fock determinant: closed form
+    hf = np.zeros(S.dim, complex)
+    hf[So.index(oracle.hf_config(6, 3, 3))[0]] = 1.0
+    r = ps.expect(H, S, _to_dev(hf, dt)).cpu().numpy()
+    assert abs(r[0] - oracle.hf_energy(6, h, g, 3, 3)) <= (1e-12 if dt == "c128" else 1e-6)
+
+
+def test_expect_24_qubits(ps, mol24):
+    h, g, H, R, S, So, psi = mol24
+    hf = np.zeros(S.dim, complex)
+    hf[So.index(oracle.hf_config(12, 6, 6))[0]] = 1.0
+    e_hf = oracle.hf_energy(12, h, g, 6, 6)
+    for dt, tol in (("c128", 1e-12), ("c64", 1e-6)):
+        r = ps.expect(H, S, _to_dev(hf, dt)).cpu().numpy()
+        assert abs(r[0] - e_hf) <= tol
+    r128 = ps.expect(H, S, _to_dev(psi, "c128")).cpu().numpy()
+    r64 = ps.expect(H, S, _to_dev(psi, "c64")).cpu().numpy()
+    assert abs(r128[0] - r64[0]) <= 1e-6
+    assert abs(r128[1]) <= 1e-12
+
+
+def test_expect_is_deterministic(ps, mol24):
+    h, g, H, R, S, So, psi = mol24
+    x = _to_dev(psi, "c64")
+    a = ps.expect(H, S, x).cpu().numpy()
+    b = ps.expect(H, S, x).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+# ----------------------------------------------------------------------------
+# rotation
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_rotate_pair_double_and_group(ps, dt):
+    norb = 6
+    S = ps.Sector.molecular(norb, 3, 3)
+    So = oracle.Sector.molecular(norb, 3, 3)
+    h, g, R = _mol(norb, 3, 3)
+    xs, cnt = np.unique(R.x, return_counts=True)
+    gx = xs[np.argmax(cnt * (xs != 0))]
+    sel = R.x == gx
+    grp = oracle.PauliSum(12, R.x[sel], R.z[sel], R.c[sel])
+    cases = [(ps.PauliSum.jw_fermion(12, w.pair_double_generator(norb, 0, 4)),
+              oracle.fermion_sum(12, w.pair_double_generator(norb, 0, 4))),
+             (ps.PauliSum.from_terms(12, grp.x, grp.z, grp.c.real, grp.c.imag, form=ps.XZ), grp)]
+    for G, Go in cases:
+        psi = w.random_state(S.dim, 31)
+        for theta in (0.41, -1.7):
+            x = _to_dev(psi, dt)
+            xin = x.cpu().numpy().astype(np.complex128)
+            ps.rotate(G, S, theta, x)
+            ref = oracle.rotate(So, Go, theta, xin)
+            assert _rel(x.cpu().numpy().astype(np.complex128), ref) <= TOL[dt]
+        assert G.status() == ps.OK
+
+
+def test_rotate_single_string_full_space(ps):
+    n = 9
+    P = ps.PauliSum.from_terms(n, [0b100101], [0b001100], [1.0])  # letters X0 Y2 Z3 X5
+    Po = oracle.build_sum(n, np.array([0b100101], np.uint64), np.array([0b001100], np.uint64), None,
+                          np.array([1.0]), np.array([0.0]))
+    S = ps.Sector.full(n)
+    So = oracle.Sector.full(n)
+    psi = w.random_state(1 << n, 4)
+    Ppsi = oracle.apply(So, Po, psi)
+    for theta in (0.3, math.pi / 2):
+        x = _to_dev(psi, "c128")
+        ps.rotate(P, S, theta, x)
+        ref = math.cos(theta) * psi - 1j * math.sin(theta) * Ppsi
+        assert _rel(x.cpu().numpy(), ref) <= 1e-13
+
+
+def test_rotate_diagonal_group(ps):
+    n = 8
+    zs = np.array([0b1, 0b110, 0b10010000], np.uint64)
+    P = ps.PauliSum.from_terms(n, np.zeros(3, np.uint64), zs, [0.3, -0.7, 0.25])
+    Po = oracle.build_sum(n, np.zeros(3, np.uint64), zs, None, np.array([0.3, -0.7, 0.25]), np.zeros(3))
+    S = ps.Sector.full(n)
+    So = oracle.Sector.full(n)
+    psi = w.random_state(1 << n, 5)
+    x = _to_dev(psi, "c128")
+    ps.rotate(P, S, 0.9, x)
+    assert _rel(x.cpu().numpy(), oracle.rotate(So, Po, 0.9, psi)) <= 1e-12
+
+
+def test_rotate_errors(ps):
+    norb = 4
+    S = ps.Sector.molecular(norb, 2, 2)
+    Go = oracle.fermion_sum(8, w.pair_double_generator(norb, 0, 2))
+    # one JW string of a pair double leaks out of the sector: device status PAULI_ESECTOR
+    one = ps.PauliSum.from_terms(8, Go.x[:1], Go.z[:1], Go.c[:1].real, Go.c[:1].imag, form=ps.XZ)
+    x = _to_dev(w.random_state(S.dim, 6), "c128")
+    ps.rotate(one, S, 0.3, x)
+    assert one.status() == ps.ESECTOR
+    assert one.status() == ps.OK  # reading clears the word
+    # two X masks
+    two = ps.PauliSum.from_terms(8, [3, 5], [0, 0], [1.0, 1.0])
+    with pytest.raises(ps.PauliError) as e:
+        ps.rotate(two, S, 0.3, x)
+    assert e.value.code == ps.EINVAL
+    # non-Hermitian generator
+    nh = ps.PauliSum.from_terms(8, [3], [0], [0.0], [1.0])
+    with pytest.raises(ps.PauliError) as e:
+        ps.rotate(nh, ps.Sector.full(8), 0.3, _to_dev(w.random_state(256, 1), "c128"))
+    assert e.value.code == ps.ENOTHERMITIAN
