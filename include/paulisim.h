@@ -30,7 +30,7 @@
  *     distinct.
  *   - State vectors are caller-owned DEVICE arrays of interleaved complex
  *     numbers: PAULI_C64 = (float re, float im), PAULI_C128 = (double re,
- *     double im), indexed by sector index, 16-byte aligned (8-byte for C64).
+ *     double im), indexed by sector index, 16-byte aligned.
  *   - Work is enqueued on the caller's CUDA stream (`pauli_stream_t` is a
  *     cudaStream_t; NULL = legacy default stream).  Calls return once the work
  *     is enqueued unless stated otherwise.

@@ -1,0 +1,10 @@
+// apply_f32.cu -- float instantiations of the gather kernels of apply_kernels.cuh
+// (split from apply.cu so the two precisions compile in parallel).
+#include "apply_kernels.cuh"
+
+namespace ps {
+void launch_apply_f32(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out,
+                      double *partials, cudaStream_t st) {
+    launch_apply_prec<float>(cfg, p, v, in, out, partials, st);
+}
+}  // namespace ps

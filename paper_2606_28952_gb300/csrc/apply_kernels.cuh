@@ -1,0 +1,528 @@
+// apply_kernels.cuh -- operator-state kernels of the gather family (Sec. 2.4):
+//   k_apply   (H psi)_t  = sum_g psi[t ^ x_g] f_g(t),
+//             f_g(t)     = sum_{k in g} C_k (-1)^popcount(z_k & (t ^ x_g))
+//             (eq. reverse_sum / eq. sreverse_sum), with the expectation
+//             value <psi|H|psi> and ||H psi||^2 reduced in FP64 (eq. vqe_energy);
+//   k_rotate  psi <- exp(-i theta G) psi for a single-X-mask Hermitian G.
+//
+// Work decomposition.  A target t = (t_hi, t_lo) lives in a row (its high
+// half: the beta string of a molecule) and a column (its low half: the alpha
+// string).  One CTA owns one row and a tile of its columns; its threads own
+// columns, so every output element is written by exactly one thread and no
+// atomics are needed (the paper's race-free target-driven summation).
+//
+// Because the row is fixed inside a CTA, the high half of every phase
+//   (-1)^popcount(z_hi & s_hi),  s_hi = t_hi ^ x_hi(g)
+// is the same for all of the CTA's targets (the alpha/beta factorisation of
+// eq. sreverse_sum).  The plan stores each group's terms sorted by (z_lo, z_hi)
+// so that terms sharing z_lo form a segment; the CTA first folds the high-half
+// phases into one coefficient per segment,
+//   a_seg = sum_{k in seg} C_k (-1)^popcount(z_hi,k & s_hi),
+// in shared memory, and the per-target loop is then
+//   f_g(t) = sum_{seg in g} a_seg (-1)^popcount(z_lo,seg & s_lo),
+// popcount parity applied as a sign-bit flip.  The source index is
+//   off_r' + rank_hi(s_hi) D_lo^r' + rank_lo(s_lo),
+// the first two terms per (row, group) in shared memory, rank_lo from a
+// table filled with the binomial colex ranking.
+#pragma once
+#include <algorithm>
+#include <cstdlib>
+
+#include "ps_internal.cuh"
+
+namespace ps {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+__device__ __forceinline__ float flip(float a, uint32_t parity_word) {
+    return __int_as_float(__float_as_int(a) ^ (int)(parity_word << 31));
+}
+__device__ __forceinline__ double flip(double a, uint32_t parity_word) {
+    return __hiloint2double(__double2hiint(a) ^ (int)(parity_word << 31), __double2loint(a));
+}
+
+struct Geom {
+    int nblk;
+    int tile;
+    int64_t cta_off[kMaxBlocks + 1];
+    int64_t ntile[kMaxBlocks];
+};
+
+struct PlanDev {
+    int32_t P, nseg_diag;
+    const uint32_t *pc_xhi;
+    const int32_t *pc_i0;
+    const uint32_t *it_xlo;
+    const int32_t *it_s0;
+    const uint32_t *s_zlo;
+    const int32_t *s_t0;
+    const uint32_t *t_zhi;
+    const double2 *t_c64;
+    const float2 *t_c32;
+};
+
+template <typename R> __device__ __forceinline__ typename Cx<R>::T coef(const PlanDev &p, int t);
+template <> __device__ __forceinline__ float2 coef<float>(const PlanDev &p, int t) { return __ldg(p.t_c32 + t); }
+template <> __device__ __forceinline__ double2 coef<double>(const PlanDev &p, int t) { return __ldg(p.t_c64 + t); }
+
+// Decode this CTA's (block, row, column tile).
+struct RowCtx {
+    int blk;
+    uint32_t thi;
+    int64_t own_base;
+    int64_t dlo;
+    int64_t c0;
+};
+
+template <bool FULL>
+__device__ __forceinline__ RowCtx decode_row(const SectorView &v, const Geom &geo) {
+    RowCtx rc;
+    const int64_t cta = blockIdx.x;
+    int b = 0;
+    while (b + 1 < geo.nblk && geo.cta_off[b + 1] <= cta) ++b;
+    const int64_t local = cta - geo.cta_off[b];
+    const int64_t rowi = local / geo.ntile[b];
+    const int64_t tile = local - rowi * geo.ntile[b];
+    rc.blk = b;
+    rc.dlo = v.dlo[b];
+    rc.c0 = tile * geo.tile;
+    if (FULL) {
+        rc.thi = (uint32_t)rowi;
+        rc.own_base = rowi << v.n_lo;
+    } else {
+        rc.thi = v.list_hi[v.list_hi_off[v.khi[b]] + rowi];
+        rc.own_base = v.off[b] + rowi * v.dlo[b];
+    }
+    return rc;
+}
+
+// cp.async (global -> shared, no register staging)
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Error-free sum (Knuth TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+enum : int { KFULL = 0, KBLK1 = 1, KBLKN = 2 };
+
+constexpr int kSegCap = PlanLimits::kSegsPerPiece;
+constexpr int kItemCap = PlanLimits::kItemsPerPiece;
+
+template <typename R>
+struct Smem {
+    using C2 = typename Cx<R>::T;
+    // byte offsets inside one buffer
+    static __host__ __device__ size_t buf_bytes(int rw) {
+        return (size_t)rw * sizeof(C2) + (size_t)kSegCap * (sizeof(C2) + sizeof(float2) + 4) +
+               (size_t)kItemCap * sizeof(int4);
+    }
+};
+
+// One pipeline buffer: a staged source row (indexed by the low-half bit
+// pattern, zero where the pattern is outside the source block), the piece's
+// folded segment coefficients and its items.
+template <typename R>
+struct Buf {
+    using C2 = typename Cx<R>::T;
+    C2 *row;
+    C2 *a;
+    float2 *alo;   // low parts of the x = 0 group's coefficients (FP32 path)
+    int4 *item;    // {x_lo, seg begin, seg end, diagonal}
+    uint32_t *z;
+    __device__ Buf(char *base, int rw) {
+        row = reinterpret_cast<C2 *>(base);
+        a = reinterpret_cast<C2 *>(base + (size_t)rw * sizeof(C2));
+        alo = reinterpret_cast<float2 *>(reinterpret_cast<char *>(a) + (size_t)kSegCap * sizeof(C2));
+        item = reinterpret_cast<int4 *>(reinterpret_cast<char *>(alo) + (size_t)kSegCap * sizeof(float2));
+        z = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(item) + (size_t)kItemCap * sizeof(int4));
+    }
+};
+
+template <typename R, int KIND, bool REALH>
+__device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &p, int q, uint32_t thi,
+                                            const typename Cx<R>::T *__restrict__ psi, Buf<R> &B,
+                                            int *klo_req) {
+    using C2 = typename Cx<R>::T;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const uint32_t shi = thi ^ __ldg(p.pc_xhi + q);
+    int64_t base;
+    int64_t len;
+    int klo = 0;
+    if (KIND == KFULL) {
+        base = (int64_t)shi << v.n_lo;
+        len = 1ll << v.n_lo;
+    } else {
+        const int bb = v.blk_of_khi[__popc(shi)];
+        klo = v.klo[bb];
+        base = v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
+        len = v.dlo[bb];
+    }
+    // 1. source row -> shared memory, asynchronously
+    if (KIND == KFULL) {
+        if (sizeof(C2) == 16) {
+            for (int64_t r = tid; r < len; r += nth) cp_async16(B.row + r, psi + base + r);
+        } else {
+            for (int64_t r = 2 * tid; r < len; r += 2 * nth) cp_async16(B.row + r, psi + base + r);
+        }
+    } else {
+        const uint32_t *lst = v.list_lo + v.list_lo_off[klo];
+        for (int64_t r = tid; r < len; r += nth) {
+            const uint32_t pos = __ldg(lst + r);
+            if (sizeof(C2) == 16) cp_async16(B.row + pos, psi + base + r);
+            else cp_async8(B.row + pos, psi + base + r);
+        }
+    }
+    cp_async_commit();
+    // 2. items of the piece
+    const int i0 = __ldg(p.pc_i0 + q), i1 = __ldg(p.pc_i0 + q + 1);
+    const int sbase = __ldg(p.it_s0 + i0);
+    for (int it = i0 + tid; it < i1; it += nth) {
+        const int s0 = __ldg(p.it_s0 + it), s1 = __ldg(p.it_s0 + it + 1);
+        B.item[it - i0] = make_int4((int)__ldg(p.it_xlo + it), s0 - sbase, s1 - sbase, s0 < p.nseg_diag ? 1 : 0);
+    }
+    // 3. fold the high-half phases of this row into one coefficient per segment
+    const int send = __ldg(p.it_s0 + i1);
+    for (int s = sbase + tid; s < send; s += nth) {
+        const int t0 = __ldg(p.s_t0 + s), t1 = __ldg(p.s_t0 + s + 1);
+        C2 a;
+        float2 lo = make_float2(0.f, 0.f);
+        if (sizeof(R) == 4 && s < p.nseg_diag) {
+            // x = 0 group on the FP32 path: sum in FP64, keep the rounding residue
+            double ar = 0.0, ai = 0.0;
+            for (int t = t0; t < t1; ++t) {
+                const double2 c = __ldg(p.t_c64 + t);
+                const uint32_t par = __popc(__ldg(p.t_zhi + t) & shi);
+                ar += flip(c.x, par);
+                ai += flip(c.y, par);
+            }
+            a.x = (R)ar;
+            a.y = (R)ai;
+            lo = make_float2((float)(ar - (double)(float)ar), (float)(ai - (double)(float)ai));
+        } else {
+            R ar = R(0), ai = R(0);
+            for (int t = t0; t < t1; ++t) {
+                const C2 c = coef<R>(p, t);
+                const uint32_t par = __popc(__ldg(p.t_zhi + t) & shi);
+                ar += flip(c.x, par);
+                if (!REALH) ai += flip(c.y, par);
+            }
+            a.x = ar;
+            a.y = ai;
+        }
+        B.a[s - sbase] = a;
+        B.alo[s - sbase] = lo;
+        B.z[s - sbase] = __ldg(p.s_zlo + s);
+    }
+    if (KIND == KBLKN && tid == 0) *klo_req = klo;
+}
+
+template <typename R, int KIND>
+__device__ __forceinline__ int next_piece(const SectorView &v, const PlanDev &p, int q, uint32_t thi) {
+    for (++q; q < p.P; ++q) {
+        if (KIND == KFULL) break;
+        const uint32_t shi = thi ^ __ldg(p.pc_xhi + q);
+        if (v.blk_of_khi[__popc(shi)] >= 0) break;
+    }
+    return q;
+}
+
+template <typename R, int KIND, bool REALH, int TPT>
+__device__ __forceinline__ void gather_piece(const PlanDev &p, int q, const Buf<R> &B, int klo_req,
+                                             const uint32_t (&tlo)[TPT], R (&accr)[TPT], R (&acci)[TPT]) {
+    using C2 = typename Cx<R>::T;
+    const int nit = __ldg(p.pc_i0 + q + 1) - __ldg(p.pc_i0 + q);
+    for (int it = 0; it < nit; ++it) {
+        const int4 e = B.item[it];
+        uint32_t s[TPT];
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) s[j] = tlo[j] ^ (uint32_t)e.x;
+        R fr[TPT], fi[TPT];
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            fr[j] = R(0);
+            fi[j] = R(0);
+        }
+        if (sizeof(R) == 4 && e.w) {
+            // x = 0 group: compensated FP32 summation of hi / lo coefficient pairs
+            R er[TPT], ei[TPT];
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                er[j] = R(0);
+                ei[j] = R(0);
+            }
+            for (int sg = e.y; sg < e.z; ++sg) {
+                const uint32_t z = B.z[sg];
+                const C2 a = B.a[sg];
+                const float2 l = B.alo[sg];
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) {
+                    const uint32_t par = __popc(z & s[j]);
+                    float t, err;
+                    two_sum(fr[j], flip((float)a.x, par), t, err);
+                    fr[j] = t;
+                    er[j] += err + flip(l.x, par);
+                    if (!REALH) {
+                        two_sum(fi[j], flip((float)a.y, par), t, err);
+                        fi[j] = t;
+                        ei[j] += err + flip(l.y, par);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                fr[j] += er[j];
+                fi[j] += ei[j];
+            }
+        } else {
+            for (int sg = e.y; sg < e.z; ++sg) {
+                const uint32_t z = B.z[sg];
+                const C2 a = B.a[sg];
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) {
+                    const uint32_t par = __popc(z & s[j]);
+                    fr[j] += flip(a.x, par);
+                    if (!REALH) fi[j] += flip(a.y, par);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            C2 amp = B.row[s[j]];
+            if (KIND == KBLKN && __popc(s[j]) != klo_req) {
+                amp.x = R(0);
+                amp.y = R(0);
+            }
+            if (REALH) {
+                accr[j] += fr[j] * amp.x;
+                acci[j] += fr[j] * amp.y;
+            } else {
+                accr[j] += fr[j] * amp.x - fi[j] * amp.y;
+                acci[j] += fr[j] * amp.y + fi[j] * amp.x;
+            }
+        }
+    }
+}
+
+template <typename R, int KIND, bool REALH, int TPT, int NBUF>
+__global__ void __launch_bounds__(kThreads)
+k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
+        typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
+    using C2 = typename Cx<R>::T;
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int klo_req[2];
+    const int rw = 1 << v.n_lo;
+    const size_t bb = Smem<R>::buf_bytes(rw);
+    Buf<R> B0(smem, rw), B1(smem + (NBUF > 1 ? bb : 0), rw);
+    const RowCtx rc = decode_row<KIND == KFULL>(v, geo);
+    const int tid = threadIdx.x;
+
+    if (KIND != KFULL) {
+        // slots outside the source block stay zero
+        for (int r = tid; r < rw; r += kThreads) {
+            C2 zz;
+            zz.x = R(0);
+            zz.y = R(0);
+            B0.row[r] = zz;
+            if (NBUF > 1) B1.row[r] = zz;
+        }
+    }
+    uint32_t tlo[TPT];
+    bool act[TPT];
+    R accr[TPT], acci[TPT];
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) {
+        const int64_t c = rc.c0 + tid + j * kThreads;
+        act[j] = c < rc.dlo;
+        tlo[j] = 0;
+        if (act[j]) tlo[j] = (KIND == KFULL) ? (uint32_t)c : __ldg(v.list_lo + v.list_lo_off[v.klo[rc.blk]] + c);
+        accr[j] = R(0);
+        acci[j] = R(0);
+    }
+    __syncthreads();
+
+    int q = next_piece<R, KIND>(v, p, -1, rc.thi);
+    if (NBUF > 1) {
+        int c = 0;
+        if (q < p.P) stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
+        while (q < p.P) {
+            const int qn = next_piece<R, KIND>(v, p, q, rc.thi);
+            if (qn < p.P) {
+                stage_piece<R, KIND, REALH>(v, p, qn, rc.thi, psi, c ? B0 : B1, &klo_req[c ^ 1]);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            gather_piece<R, KIND, REALH, TPT>(p, q, c ? B1 : B0, klo_req[c], tlo, accr, acci);
+            __syncthreads();
+            c ^= 1;
+            q = qn;
+        }
+    } else {
+        while (q < p.P) {
+            stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
+            cp_async_wait<0>();
+            __syncthreads();
+            gather_piece<R, KIND, REALH, TPT>(p, q, B0, klo_req[0], tlo, accr, acci);
+            __syncthreads();
+            q = next_piece<R, KIND>(v, p, q, rc.thi);
+        }
+    }
+
+    // epilogue: store and / or FP64 reductions
+    double er = 0.0, ei = 0.0, h2 = 0.0, p2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) {
+        if (!act[j]) continue;
+        const int64_t idx = rc.own_base + rc.c0 + tid + j * kThreads;
+        if (flags & 1) {
+            C2 o;
+            o.x = accr[j];
+            o.y = acci[j];
+            out[idx] = o;
+        }
+        if (flags & 2) {
+            const C2 ps = psi[idx];
+            const double pr = (double)ps.x, pi = (double)ps.y;
+            const double hr = (double)accr[j], hi = (double)acci[j];
+            er += pr * hr + pi * hi;
+            ei += pr * hi - pi * hr;
+            h2 += hr * hr + hi * hi;
+            p2 += pr * pr + pi * pi;
+        }
+    }
+    if (flags & 2) {
+        __shared__ double red[4][kThreads / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            er += __shfl_down_sync(0xffffffffu, er, o);
+            ei += __shfl_down_sync(0xffffffffu, ei, o);
+            h2 += __shfl_down_sync(0xffffffffu, h2, o);
+            p2 += __shfl_down_sync(0xffffffffu, p2, o);
+        }
+        const int lane = tid & 31, warp = tid >> 5;
+        if (lane == 0) {
+            red[0][warp] = er;
+            red[1][warp] = ei;
+            red[2][warp] = h2;
+            red[3][warp] = p2;
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double sum = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) sum += red[tid][w];
+            partials[(int64_t)blockIdx.x * 4 + tid] = sum;
+        }
+    }
+}
+
+
+int env_int(const char *name, int dflt) {
+    const char *e = std::getenv(name);
+    if (!e || !*e) return dflt;
+    return std::atoi(e);
+}
+
+Geom make_geom(const SectorView &v, int tile) {
+    Geom g;
+    g.nblk = v.nblk;
+    g.tile = tile;
+    g.cta_off[0] = 0;
+    for (int b = 0; b < v.nblk; ++b) {
+        const int64_t nt = (v.dlo[b] + tile - 1) / tile;
+        g.ntile[b] = nt > 0 ? nt : 1;
+        const int64_t ctas = (v.dlo[b] > 0) ? v.dhi[b] * nt : 0;
+        g.cta_off[b + 1] = g.cta_off[b] + ctas;
+    }
+    return g;
+}
+
+PlanDev plan_dev(const Plan &p) {
+    PlanDev d;
+    d.P = (int32_t)p.P;
+    d.nseg_diag = p.nseg_diag;
+    d.pc_xhi = p.pc_xhi;
+    d.pc_i0 = p.pc_i0;
+    d.it_xlo = p.it_xlo;
+    d.it_s0 = p.it_s0;
+    d.s_zlo = p.s_zlo;
+    d.s_t0 = p.s_t0;
+    d.t_zhi = p.t_zhi;
+    d.t_c64 = p.t_c64;
+    d.t_c32 = p.t_c32;
+    return d;
+}
+
+template <typename R, int KIND, bool REALH, int TPT, int NBUF>
+void launch_one(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, const PlanDev &pd, const void *in,
+                void *out, double *partials, int flags, cudaStream_t st) {
+    using C2 = typename Cx<R>::T;
+    auto kern = k_apply<R, KIND, REALH, TPT, NBUF>;
+    static size_t attr_bytes = 48 * 1024;  // dynamic shared memory this kernel is opted in for
+    if (cfg.smem > attr_bytes) {
+        PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
+        attr_bytes = cfg.smem;
+    }
+    kern<<<(unsigned)cfg.nct, kThreads, cfg.smem, st>>>(v, geo, pd, static_cast<const C2 *>(in),
+                                                         static_cast<C2 *>(out), partials, flags);
+    PS_LAUNCH_CHECK();
+}
+
+template <typename R, int KIND, bool REALH>
+void launch_kind(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, const PlanDev &pd, const void *in,
+                 void *out, double *partials, int flags, cudaStream_t st) {
+#define PS_L(T, N) launch_one<R, KIND, REALH, T, N>(cfg, v, geo, pd, in, out, partials, flags, st)
+    if (cfg.nbuf == 2) {
+        switch (cfg.tpt) {
+            case 4: PS_L(4, 2); break;
+            case 2: PS_L(2, 2); break;
+            default: PS_L(1, 2); break;
+        }
+    } else {
+        switch (cfg.tpt) {
+            case 4: PS_L(4, 1); break;
+            case 2: PS_L(2, 1); break;
+            default: PS_L(1, 1); break;
+        }
+    }
+#undef PS_L
+}
+
+template <typename R>
+void launch_apply_prec(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out,
+                       double *partials, cudaStream_t st) {
+    const Geom geo = make_geom(v, cfg.tpt * kThreads);
+    const PlanDev pd = plan_dev(p);
+    const int flags = (out ? 1 : 0) | (partials ? 2 : 0);
+    const int kind = v.kind == PAULI_SECTOR_FULL ? KFULL : (v.nblk == 1 ? KBLK1 : KBLKN);
+    if (p.real) {
+        if (kind == KFULL) launch_kind<R, KFULL, true>(cfg, v, geo, pd, in, out, partials, flags, st);
+        else if (kind == KBLK1) launch_kind<R, KBLK1, true>(cfg, v, geo, pd, in, out, partials, flags, st);
+        else launch_kind<R, KBLKN, true>(cfg, v, geo, pd, in, out, partials, flags, st);
+    } else {
+        if (kind == KFULL) launch_kind<R, KFULL, false>(cfg, v, geo, pd, in, out, partials, flags, st);
+        else if (kind == KBLK1) launch_kind<R, KBLK1, false>(cfg, v, geo, pd, in, out, partials, flags, st);
+        else launch_kind<R, KBLKN, false>(cfg, v, geo, pd, in, out, partials, flags, st);
+    }
+}
+
+}  // namespace
+}  // namespace ps

@@ -258,15 +258,6 @@ __global__ void k_plan_group_segs(int64_t S, const int64_t *seg_group, int32_t *
     if (s == 0 || seg_group[s] != seg_group[s - 1]) g_s0[seg_group[s]] = (int32_t)s;
 }
 
-__global__ void k_plan_groups(int64_t G, int n_lo, const uint64_t *gx, uint32_t *g_xlo,
-                              uint32_t *g_xhi) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
-    uint64_t lomask = (n_lo >= 64) ? ~0ull : ((1ull << n_lo) - 1ull);
-    g_xlo[g] = (uint32_t)(gx[g] & lomask);
-    g_xhi[g] = (uint32_t)(gx[g] >> n_lo);
-}
-
 __global__ void k_shift_right(int64_t m, const uint64_t *in, int sh, uint64_t *out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) out[i] = (sh >= 64) ? 0ull : (in[i] >> sh);
@@ -450,10 +441,9 @@ void jw_fermion_raw_device(int n, int nterms, const int *nf, const int *modes, c
 }
 
 void free_plan(const Allocator &al, Plan &p) {
-    dev_free(al, p.g_xlo); dev_free(al, p.g_xhi); dev_free(al, p.g_s0);
+    dev_free(al, p.pc_xhi); dev_free(al, p.pc_i0); dev_free(al, p.it_xlo); dev_free(al, p.it_s0);
     dev_free(al, p.s_zlo); dev_free(al, p.s_t0);
     dev_free(al, p.t_zhi); dev_free(al, p.t_c64); dev_free(al, p.t_c32);
-    dev_free(al, p.b_i0); dev_free(al, p.it_g); dev_free(al, p.it_s0); dev_free(al, p.s_xhi);
     dev_free(al, p.partials);
     p = Plan();
 }
@@ -475,19 +465,14 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
     p.M = M;
     p.G = G;
     p.real = h->real;
-    p.g_xlo = static_cast<uint32_t *>(dev_alloc(al, (G > 0 ? G : 1) * sizeof(uint32_t)));
-    p.g_xhi = static_cast<uint32_t *>(dev_alloc(al, (G > 0 ? G : 1) * sizeof(uint32_t)));
-    p.g_s0 = static_cast<int32_t *>(dev_alloc(al, (G + 1) * sizeof(int32_t)));
     p.t_zhi = static_cast<uint32_t *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(uint32_t)));
     p.t_c64 = static_cast<double2 *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(double2)));
     p.t_c32 = static_cast<float2 *>(dev_alloc(al, (M > 0 ? M : 1) * sizeof(float2)));
-    std::vector<int32_t> hs0(G + 1, 0);
+    std::vector<int32_t> g_s0(G + 1, 0);
     int64_t S = 0;
     if (M > 0) {
-        k_plan_groups<<<nblk(G), 256, 0, st>>>(G, n_lo, h->gx, p.g_xlo, p.g_xhi);
-        PS_LAUNCH_CHECK();
         DevBuf<int64_t> gid(al, M), perm(al, M), head(al, M), sid(al, M);
-        DevBuf<uint64_t> khi(al, M), klo(al, M);
+        DevBuf<uint64_t> khi(al, M), klo(al, M), seg_key(al, M);
         k_fill_group_id<<<nblk(G), 256, 0, st>>>(G, h->gstart, gid.p);
         PS_LAUNCH_CHECK();
         k_plan_keys<<<nblk(M), 256, 0, st>>>(M, n_lo, n_hi, gid.p, h->z, khi.p, klo.p);
@@ -497,8 +482,7 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
         radix_sort_keys(khi.p, klo.p, perm.p, M, gbits, h->n, al, st);
         k_plan_terms<<<nblk(M), 256, 0, st>>>(M, n_hi, klo.p, perm.p, h->c, p.t_zhi, p.t_c64, p.t_c32);
         PS_LAUNCH_CHECK();
-        // segments: runs of equal (group, z_lo); z_lo = klo >> n_hi
-        DevBuf<uint64_t> seg_key(al, M);
+        // segments: runs of equal (group, z_lo) in the re-sorted order
         k_shift_right<<<nblk(M), 256, 0, st>>>(M, klo.p, n_hi, seg_key.p);
         PS_LAUNCH_CHECK();
         k_head_flags<<<nblk(M), 256, 0, st>>>(khi.p, seg_key.p, M, head.p);
@@ -512,69 +496,66 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
         p.s_zlo = static_cast<uint32_t *>(dev_alloc(al, S * sizeof(uint32_t)));
         p.s_t0 = static_cast<int32_t *>(dev_alloc(al, (S + 1) * sizeof(int32_t)));
         DevBuf<int64_t> seg_group(al, S);
+        DevBuf<int32_t> d_gs0(al, G + 1);
         k_plan_segments<<<nblk(M), 256, 0, st>>>(M, n_hi, head.p, sid.p, khi.p, klo.p, p.s_t0, p.s_zlo,
                                                   seg_group.p);
         PS_LAUNCH_CHECK();
         int32_t m32 = (int32_t)M;
         PS_CUDA(cudaMemcpyAsync(p.s_t0 + S, &m32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        k_plan_group_segs<<<nblk(S), 256, 0, st>>>(S, seg_group.p, p.g_s0);
+        k_plan_group_segs<<<nblk(S), 256, 0, st>>>(S, seg_group.p, d_gs0.p);
         PS_LAUNCH_CHECK();
-        int32_t s32 = (int32_t)S;
-        PS_CUDA(cudaMemcpyAsync(p.g_s0 + G, &s32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        PS_CUDA(cudaMemcpyAsync(hs0.data(), p.g_s0, (G + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(g_s0.data(), d_gs0.p, G * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         PS_CUDA(cudaStreamSynchronize(st));
+        g_s0[G] = (int32_t)S;
     } else {
         p.s_zlo = static_cast<uint32_t *>(dev_alloc(al, sizeof(uint32_t)));
         p.s_t0 = static_cast<int32_t *>(dev_alloc(al, sizeof(int32_t)));
         PS_CUDA(cudaMemset(p.s_t0, 0, sizeof(int32_t)));
-        PS_CUDA(cudaMemset(p.g_s0, 0, sizeof(int32_t)));
     }
     p.S = S;
-    // items: (group, contiguous segment range) of at most kSegsPerBatch segments;
-    // batches: consecutive items with at most kGroupsPerBatch items and
-    // kSegsPerBatch segments in total.
-    std::vector<int32_t> it_g, it_s0, b_i0;
-    b_i0.push_back(0);
-    int items_in_batch = 0, segs_in_batch = 0;
+    std::vector<uint64_t> gx(G > 0 ? G : 1);
+    if (G > 0) PS_CUDA(cudaMemcpy(gx.data(), h->gx, G * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    const uint64_t lomask = (n_lo >= 64) ? ~0ull : ((1ull << n_lo) - 1ull);
+    // pieces of consecutive groups with one x_hi; items of at most kSegsPerPiece segments
+    std::vector<uint32_t> pc_xhi, it_xlo;
+    std::vector<int32_t> pc_i0, it_s0;
+    int items_in_piece = 0, segs_in_piece = 0;
+    uint64_t cur_xhi = ~0ull;
     for (int64_t g = 0; g < G; ++g) {
-        int32_t s = hs0[g];
-        const int32_t se = hs0[g + 1];
+        const uint64_t xhi = gx[g] >> n_lo, xlo = gx[g] & lomask;
+        int32_t s = g_s0[g];
+        const int32_t se = g_s0[g + 1];
         while (s < se) {
-            int32_t take = std::min<int32_t>(se - s, PlanLimits::kSegsPerBatch);
-            if (items_in_batch == PlanLimits::kGroupsPerBatch ||
-                segs_in_batch + take > PlanLimits::kSegsPerBatch) {
-                b_i0.push_back((int32_t)it_g.size());
-                items_in_batch = 0;
-                segs_in_batch = 0;
+            const int32_t take = std::min<int32_t>(se - s, PlanLimits::kSegsPerPiece);
+            if (pc_xhi.empty() || xhi != cur_xhi || items_in_piece == PlanLimits::kItemsPerPiece ||
+                segs_in_piece + take > PlanLimits::kSegsPerPiece) {
+                pc_xhi.push_back((uint32_t)xhi);
+                pc_i0.push_back((int32_t)it_xlo.size());
+                cur_xhi = xhi;
+                items_in_piece = 0;
+                segs_in_piece = 0;
             }
-            it_g.push_back((int32_t)g);
+            it_xlo.push_back((uint32_t)xlo);
             it_s0.push_back(s);
-            ++items_in_batch;
-            segs_in_batch += take;
+            ++items_in_piece;
+            segs_in_piece += take;
             s += take;
         }
     }
+    pc_i0.push_back((int32_t)it_xlo.size());
     it_s0.push_back((int32_t)S);
-    if (!it_g.empty()) b_i0.push_back((int32_t)it_g.size());
-    p.nbatch = (int64_t)b_i0.size() - 1;
-    p.nitem = (int64_t)it_g.size();
-    p.h_b_i0 = b_i0;
-    p.b_i0 = static_cast<int32_t *>(dev_alloc(al, b_i0.size() * sizeof(int32_t)));
-    p.it_g = static_cast<int32_t *>(dev_alloc(al, (it_g.empty() ? 1 : it_g.size()) * sizeof(int32_t)));
-    p.it_s0 = static_cast<int32_t *>(dev_alloc(al, it_s0.size() * sizeof(int32_t)));
-    PS_CUDA(cudaMemcpy(p.b_i0, b_i0.data(), b_i0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    if (!it_g.empty())
-        PS_CUDA(cudaMemcpy(p.it_g, it_g.data(), it_g.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    PS_CUDA(cudaMemcpy(p.it_s0, it_s0.data(), it_s0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    // x_hi of each segment's group (phase 1 of the apply kernel reads it per segment)
-    {
-        std::vector<uint32_t> hxhi(G > 0 ? G : 1), sx(S > 0 ? S : 1);
-        if (G > 0) PS_CUDA(cudaMemcpy(hxhi.data(), p.g_xhi, G * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-        for (int64_t g = 0; g < G; ++g)
-            for (int32_t s = hs0[g]; s < hs0[g + 1]; ++s) sx[s] = hxhi[g];
-        p.s_xhi = static_cast<uint32_t *>(dev_alloc(al, (S > 0 ? S : 1) * sizeof(uint32_t)));
-        if (S > 0) PS_CUDA(cudaMemcpy(p.s_xhi, sx.data(), S * sizeof(uint32_t), cudaMemcpyHostToDevice));
-    }
+    p.P = (int64_t)pc_xhi.size();
+    p.I = (int64_t)it_xlo.size();
+    p.nseg_diag = (G > 0 && gx[0] == 0) ? g_s0[1] - g_s0[0] : 0;
+    auto upload = [&](const void *src, size_t bytes) {
+        void *d = dev_alloc(al, bytes > 0 ? bytes : 4);
+        if (bytes > 0) PS_CUDA(cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
+        return d;
+    };
+    p.pc_xhi = static_cast<uint32_t *>(upload(pc_xhi.data(), pc_xhi.size() * sizeof(uint32_t)));
+    p.pc_i0 = static_cast<int32_t *>(upload(pc_i0.data(), pc_i0.size() * sizeof(int32_t)));
+    p.it_xlo = static_cast<uint32_t *>(upload(it_xlo.data(), it_xlo.size() * sizeof(uint32_t)));
+    p.it_s0 = static_cast<int32_t *>(upload(it_s0.data(), it_s0.size() * sizeof(int32_t)));
     h->plans[h->nplans] = p;
     return h->plans[h->nplans++];
 }

@@ -100,38 +100,34 @@ struct SectorView {
 // apply plan: the canonical sum re-laid out for one sector split (rows = high
 // n - n_lo qubits, columns = low n_lo qubits)
 // ---------------------------------------------------------------------------
+// Layout (all device arrays):
+//   piece p   : consecutive groups sharing x_hi (so one source row per CTA row),
+//               at most kItemsPerPiece items and kSegsPerPiece segments
+//   item i    : one group, or a slice of a group's segments
+//   segment s : terms of one group with equal z_lo, sorted by (z_lo, z_hi)
 struct Plan {
     int n_lo = -1;
     int64_t G = 0, S = 0, M = 0;      // groups, segments, terms
-    int64_t nbatch = 0;
+    int64_t P = 0, I = 0;             // pieces, items
+    int32_t nseg_diag = 0;            // segments [0, nseg_diag) belong to the x = 0 group
     bool real = true;                  // every C_k real
-    // per group (canonical group order, i.e. ascending x)
-    uint32_t *g_xlo = nullptr, *g_xhi = nullptr;
-    int32_t *g_s0 = nullptr;           // [G+1] segment range
-    // per segment: equal z_lo within a group, terms sorted by (z_lo, z_hi)
-    uint32_t *s_zlo = nullptr;
+    uint32_t *pc_xhi = nullptr;        // [P]
+    int32_t *pc_i0 = nullptr;          // [P+1] item range
+    uint32_t *it_xlo = nullptr;        // [I]
+    int32_t *it_s0 = nullptr;          // [I+1] segment range
+    uint32_t *s_zlo = nullptr;         // [S]
     int32_t *s_t0 = nullptr;           // [S+1] term range
-    // per term (segment order)
-    uint32_t *t_zhi = nullptr;
-    double2 *t_c64 = nullptr;          // FP64 coefficients
-    float2 *t_c32 = nullptr;           // FP32 coefficients
-    uint32_t *s_xhi = nullptr;         // [S] x_hi of the segment's group
-    // items: (group, contiguous segment range) pieces; batches: consecutive
-    // items whose segments fit the apply kernel's shared memory
-    int64_t nitem = 0;
-    int32_t *it_g = nullptr;           // [nitem] group of each item
-    int32_t *it_s0 = nullptr;          // [nitem+1] segment range of each item
-    int32_t *b_i0 = nullptr;           // [nbatch+1] item range of each batch
-    std::vector<int32_t> h_b_i0;
+    uint32_t *t_zhi = nullptr;         // [M] (segment order)
+    double2 *t_c64 = nullptr;          // [M] FP64 coefficients
+    float2 *t_c32 = nullptr;           // [M] FP32 coefficients
     // reduction scratch for pauli_expect
     double *partials = nullptr;
     int64_t partials_cap = 0;
-    void *owner_alloc_ctx = nullptr;
 };
 
 struct PlanLimits {
-    static constexpr int kGroupsPerBatch = 128;
-    static constexpr int kSegsPerBatch = 1024;
+    static constexpr int kItemsPerPiece = 64;
+    static constexpr int kSegsPerPiece = 512;
 };
 
 }  // namespace ps
@@ -198,6 +194,13 @@ void sector_unrank(const SectorView &v, const int64_t *idx, int64_t n, uint64_t 
                    cudaStream_t st);
 
 // apply.cu
+struct ApplyCfg {
+    int tpt = 1;        // targets (columns) per thread
+    int nbuf = 1;       // staged source rows in flight (1 or 2)
+    size_t smem = 0;    // dynamic shared memory per CTA
+    int64_t nct = 0;    // CTAs of one launch
+};
+ApplyCfg apply_config(const SectorView &v, int dtype);
 void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *psi_in,
                   void *psi_out, int dtype, double *partials, cudaStream_t st);
 void launch_reduce(const double *partials, int64_t nparts, double *result, cudaStream_t st);

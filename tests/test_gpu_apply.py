@@ -110,7 +110,9 @@ def test_apply_edge_cases(ps):
         So = oracle.Sector.molecular(4, na, nb)
         psi = w.random_state(S.dim, 2)
         out = ps.apply(H, S, _to_dev(psi, "c128")).cpu().numpy()
-        assert _rel(out, oracle.apply(So, R, psi)) <= 1e-12
+        ref = oracle.apply(So, R, psi)
+        # the vacuum row is pure rounding noise of cancelling terms: bound by the operator scale
+        assert np.linalg.norm(out - ref) <= 1e-12 * max(np.linalg.norm(ref), np.abs(R.c).sum())
     # in-place (aliased) apply is rejected
     S = ps.Sector.molecular(4, 2, 2)
     y = _to_dev(w.random_state(S.dim, 3), "c128")
