@@ -191,6 +191,32 @@ int pauli_apply(pauli_sum *H, const pauli_sector *s, const void *psi_in, void *p
 int pauli_expect(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype, double *result,
                  void *hpsi_out, pauli_stream_t st);
 
+/* pauli_expect without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot have device memory allocated on
+ * their behalf -- programs whose GPU memory is entirely owned by another
+ * allocator (a framework's caching pool that reserves the device), and
+ * latency-critical loops where a cudaMalloc / cudaFree (which can synchronise
+ * the whole device) is not acceptable.
+ * Same arguments, results and precision as pauli_expect.  Its per-block
+ * partial sums live in one static device array of 65,536 blocks x 4 doubles
+ * (2 MiB, held on every GPU that loads the library until the process exits)
+ * instead of memory the library allocates:
+ *   - the plan for this sector's split must already exist: call
+ *     pauli_prepare(H, s) (which allocates) once beforehand, otherwise
+ *     PAULI_EINVAL;
+ *   - a sector whose launch needs more than 65,536 blocks gets
+ *     PAULI_EUNSUPPORTED (the 24-qubit (6a,6b) sector needs 924);
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - every call uses the same array, and each block overwrites its own
+ *     partials before they are read, so no state from an earlier call
+ *     matters; calls that overlap on the GPU (different streams, no ordering
+ *     between them) race on the array and must not be issued.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. */
+int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype,
+                         double *result, void *hpsi_out, pauli_stream_t st);
+
 /* psi <- exp(-i theta G) psi in place, for a Hermitian G with ONE X mask x
  * (a single group; Sec. 2.5 and the Trotter factors exp(theta tau) of
  * Sec. 3.2 with G = i tau).  G maps each pair {t, t XOR x} onto itself with

@@ -56,6 +56,7 @@ SIGNATURES = {
     "pauli_prepare": (_i32, [_vp, _vp]),
     "pauli_apply": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
     "pauli_expect": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "pauli_expect_noalloc": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "pauli_rotate": (_i32, [_vp, _vp, _dbl, _vp, _i32, _vp]),
     "pauli_status": (_i32, [_vp, _vp, _vp]),
 }
@@ -312,6 +313,22 @@ def expect(H: PauliSum, s: Sector, psi, hpsi_out=None, result=None, stream=None)
         hp = C.c_void_p(hpsi_out.data_ptr())
     _check(lib().pauli_expect(H._h, s._h, C.c_void_p(psi.data_ptr()), _dtype_code(psi),
                               C.c_void_p(result.data_ptr()), hp, _stream_ptr(stream)))
+    return result
+
+
+def expect_noalloc(H: PauliSum, s: Sector, psi, result, hpsi_out=None, stream=None):
+    """pauli_expect with its scratch in a static device array: allocates nothing.
+
+    For callers that cannot have device memory allocated for them.  Needs
+    prepare(H, s) beforehand and a caller-provided ``result`` (float64[4] on the
+    device); calls that overlap on the GPU race on the shared scratch."""
+    _check_state(psi, s.dim, "psi")
+    hp = None
+    if hpsi_out is not None:
+        _check_state(hpsi_out, s.dim, "hpsi_out")
+        hp = C.c_void_p(hpsi_out.data_ptr())
+    _check(lib().pauli_expect_noalloc(H._h, s._h, C.c_void_p(psi.data_ptr()), _dtype_code(psi),
+                                      C.c_void_p(result.data_ptr()), hp, _stream_ptr(stream)))
     return result
 
 

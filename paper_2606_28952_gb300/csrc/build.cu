@@ -448,6 +448,12 @@ void free_plan(const Allocator &al, Plan &p) {
     p = Plan();
 }
 
+Plan *find_plan(pauli_sum *h, int n_lo) {
+    for (int i = 0; i < h->nplans; ++i)
+        if (h->plans[i].n_lo == n_lo) return &h->plans[i];
+    return nullptr;
+}
+
 Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
     for (int i = 0; i < h->nplans; ++i)
         if (h->plans[i].n_lo == n_lo) return h->plans[i];

@@ -177,6 +177,7 @@ void jw_fermion_raw_device(int n, int nterms, const int *nf, const int *modes, c
                            DevBuf<uint64_t> &x, DevBuf<uint64_t> &z, DevBuf<double2> &c,
                            int64_t &count, cudaStream_t st);
 Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st);
+Plan *find_plan(pauli_sum *h, int n_lo);  // existing plan or nullptr; never builds
 void free_plan(const Allocator &al, Plan &p);
 
 // scan.cu
