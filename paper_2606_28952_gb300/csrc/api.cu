@@ -151,8 +151,20 @@ void check_integrals(int norb, const double *h, const double *g) {
 
 Plan &ensure_plan(pauli_sum *H, const pauli_sector *s, cudaStream_t st, bool need_partials) {
     Plan &p = get_plan(H, s->v.n_lo, st);
+    // partial vectors of split launches (the split count depends on the dtype)
+    const int64_t split_bytes = std::max(apply_split_elems(p, s->v, PAULI_C64) * 8,
+                                         apply_split_elems(p, s->v, PAULI_C128) * 16);
+    if (p.split_cap < split_bytes) {
+        PS_CUDA(cudaStreamSynchronize(st));
+        dev_free(H->al, p.split_buf);
+        p.split_buf = nullptr;
+        p.split_cap = 0;
+        p.split_buf = dev_alloc(H->al, (size_t)split_bytes);
+        p.split_cap = split_bytes;
+    }
     if (need_partials) {
-        const int64_t nct = apply_num_ctas(p, s->v, PAULI_C128);
+        const int64_t nct = std::max(apply_num_ctas(p, s->v, PAULI_C128, true),
+                                     apply_num_ctas(p, s->v, PAULI_C128, false));
         if (p.partials_cap < nct) {
             PS_CUDA(cudaStreamSynchronize(st));
             dev_free(H->al, p.partials);
@@ -475,7 +487,7 @@ int pauli_expect(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype
         }
         cudaStream_t cs = (cudaStream_t)st;
         Plan &p = ensure_plan(H, s, cs, true);
-        const int64_t nct = apply_num_ctas(p, s->v, dtype);
+        const int64_t nct = apply_num_ctas(p, s->v, dtype, true);
         if (nct == 0) {
             PS_CUDA(cudaMemsetAsync(result, 0, 4 * sizeof(double), cs));
             return;

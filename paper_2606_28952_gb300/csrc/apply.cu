@@ -4,9 +4,9 @@
 
 namespace ps {
 void launch_apply_f32(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out,
-                      double *partials, cudaStream_t st);
+                      double *partials, void *split_buf, cudaStream_t st);
 void launch_apply_f64(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out,
-                      double *partials, cudaStream_t st);
+                      double *partials, void *split_buf, cudaStream_t st);
 namespace {
 
 // Fixed-order FP64 reduction of [nparts][4] partials into result[4].
@@ -120,12 +120,20 @@ k_rotate(SectorView v, Geom geo, int64_t m, uint64_t x, const uint64_t *__restri
 // 227 KB of shared memory per block on sm_103a, less room for the kernel's static arrays
 constexpr size_t kMaxDynSmem = 226 * 1024;
 
-ApplyCfg apply_config(const SectorView &v, int dtype) {
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        PS_CUDA(cudaGetDevice(&dev));
+        PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
+ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split) {
     ApplyCfg c;
-    const size_t esize = dtype == PAULI_C64 ? sizeof(float2) : sizeof(double2);
     const int rw = 1 << v.n_lo;
     const size_t bb = dtype == PAULI_C64 ? Smem<float>::buf_bytes(rw) : Smem<double>::buf_bytes(rw);
-    (void)esize;
     int64_t mx = 0;
     for (int b = 0; b < v.nblk; ++b) mx = std::max(mx, v.dlo[b]);
     // measured on the 24-qubit molecule (D_lo = 924): 4 columns per thread and a
@@ -133,32 +141,65 @@ ApplyCfg apply_config(const SectorView &v, int dtype) {
     int tpt = mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1);
     tpt = env_int("PAULISIM_TPT", tpt);
     if (tpt != 1 && tpt != 2 && tpt != 4) tpt = 1;
-    int nbuf = 1;
-    nbuf = env_int("PAULISIM_NBUF", nbuf);
+    int nbuf = env_int("PAULISIM_NBUF", 1);
     if (nbuf != 1 && nbuf != 2) nbuf = 1;
     if (nbuf * bb > kMaxDynSmem) nbuf = 1;
     c.tpt = tpt;
     c.nbuf = nbuf;
     c.smem = nbuf * bb;
-    c.nct = make_geom(v, tpt * kThreads).cta_off[v.nblk];
+    c.base_nct = make_geom(v, tpt * kThreads).cta_off[v.nblk];
+    // Too few rows for the GPU: split each row's pieces into nsplit balanced
+    // ranges (by the plan's per-piece work estimate) so that a launch has about
+    // four waves of CTAs; k_combine adds the partial vectors in a fixed order.
+    int nsplit = 1;
+    if (allow_split && c.base_nct > 0 && p.P > 1) {
+        const int per_sm = std::max<int>(1, std::min<int>(2048 / kThreads, (int)((228 * 1024) / (c.smem + 2048))));
+        const int64_t slots = (int64_t)num_sms() * per_sm;
+        if (c.base_nct < 4 * slots) nsplit = (int)((4 * slots + c.base_nct - 1) / c.base_nct);
+        nsplit = env_int("PAULISIM_SPLIT", nsplit);
+        nsplit = std::max(1, std::min<int>({nsplit, kMaxSplit, (int)std::max<int64_t>(1, p.P / 8)}));
+    }
+    c.nsplit = nsplit;
+    c.split_p0.assign(nsplit + 1, 0);
+    const int64_t W = p.h_pc_cumw.empty() ? 0 : p.h_pc_cumw.back();
+    for (int k = 1; k < nsplit; ++k) {
+        const int64_t target = W * k / nsplit;
+        const int32_t q = (int32_t)(std::lower_bound(p.h_pc_cumw.begin(), p.h_pc_cumw.end(), target) - p.h_pc_cumw.begin());
+        c.split_p0[k] = std::max(c.split_p0[k - 1], std::min<int32_t>(q, (int32_t)p.P));
+    }
+    c.split_p0[nsplit] = (int32_t)p.P;
+    c.nct = c.base_nct * nsplit;
+    c.combine_nct = nsplit > 1 ? (v.dim + kThreads - 1) / kThreads : 0;
     return c;
 }
 
-int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype) {
-    (void)p;
-    return apply_config(v, dtype).nct;
+int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow_split) {
+    const ApplyCfg c = apply_config(p, v, dtype, allow_split);
+    return c.nsplit > 1 ? c.combine_nct : c.base_nct;
+}
+
+int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype) {
+    const ApplyCfg c = apply_config(p, v, dtype, true);
+    return c.nsplit > 1 ? (int64_t)c.nsplit * v.dim : 0;
 }
 
 void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *psi_in, void *psi_out,
-                  int dtype, double *partials, cudaStream_t st) {
+                  int dtype, double *partials, cudaStream_t st, bool allow_split) {
     (void)H;
-    const ApplyCfg cfg = apply_config(v, dtype);
+    const ApplyCfg cfg = apply_config(p, v, dtype, allow_split);
     if (cfg.nct == 0) return;
     PS_CHECK(cfg.nct < (1ll << 31), PAULI_EUNSUPPORTED, "apply: too many thread blocks");
     PS_CHECK(cfg.smem <= kMaxDynSmem, PAULI_EUNSUPPORTED,
              "apply: the low half of the sector split is too wide for shared-memory staging");
-    if (dtype == PAULI_C64) launch_apply_f32(cfg, p, v, psi_in, psi_out, partials, st);
-    else launch_apply_f64(cfg, p, v, psi_in, psi_out, partials, st);
+    void *split_buf = nullptr;
+    if (cfg.nsplit > 1) {
+        const int64_t need = (int64_t)cfg.nsplit * v.dim * (dtype == PAULI_C64 ? 8 : 16);
+        PS_CHECK(p.split_buf != nullptr && p.split_cap >= need, PAULI_EINVAL,
+                 "apply: the plan's split buffer is missing (internal)");
+        split_buf = p.split_buf;
+    }
+    if (dtype == PAULI_C64) launch_apply_f32(cfg, p, v, psi_in, psi_out, partials, split_buf, st);
+    else launch_apply_f64(cfg, p, v, psi_in, psi_out, partials, split_buf, st);
 }
 
 void launch_reduce(const double *partials, int64_t nparts, double *result, cudaStream_t st) {

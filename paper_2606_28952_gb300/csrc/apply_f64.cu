@@ -4,7 +4,7 @@
 
 namespace ps {
 void launch_apply_f64(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out,
-                      double *partials, cudaStream_t st) {
-    launch_apply_prec<double>(cfg, p, v, in, out, partials, st);
+                      double *partials, void *split_buf, cudaStream_t st) {
+    launch_apply_prec<double>(cfg, p, v, in, out, partials, split_buf, st);
 }
 }  // namespace ps

@@ -46,11 +46,17 @@ __device__ __forceinline__ double flip(double a, uint32_t parity_word) {
     return __hiloint2double(__double2hiint(a) ^ (int)(parity_word << 31), __double2loint(a));
 }
 
+constexpr int kMaxSplit = 16;
+
 struct Geom {
     int nblk;
     int tile;
     int64_t cta_off[kMaxBlocks + 1];
     int64_t ntile[kMaxBlocks];
+    // each (row, column tile) is split into nsplit CTAs over consecutive piece
+    // ranges [split_p0[k], split_p0[k+1]); their partial sums are added by k_combine
+    int nsplit;
+    int32_t split_p0[kMaxSplit + 1];
 };
 
 struct PlanDev {
@@ -77,12 +83,14 @@ struct RowCtx {
     int64_t own_base;
     int64_t dlo;
     int64_t c0;
+    int split;
 };
 
 template <bool FULL>
 __device__ __forceinline__ RowCtx decode_row(const SectorView &v, const Geom &geo) {
     RowCtx rc;
-    const int64_t cta = blockIdx.x;
+    const int64_t cta = (int64_t)blockIdx.x / geo.nsplit;
+    rc.split = (int)((int64_t)blockIdx.x - cta * geo.nsplit);
     int b = 0;
     while (b + 1 < geo.nblk && geo.cta_off[b + 1] <= cta) ++b;
     const int64_t local = cta - geo.cta_off[b];
@@ -235,8 +243,8 @@ __device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &
 }
 
 template <typename R, int KIND>
-__device__ __forceinline__ int next_piece(const SectorView &v, const PlanDev &p, int q, uint32_t thi) {
-    for (++q; q < p.P; ++q) {
+__device__ __forceinline__ int next_piece(const SectorView &v, const PlanDev &p, int q, uint32_t thi, int pend) {
+    for (++q; q < pend; ++q) {
         if (KIND == KFULL) break;
         const uint32_t shi = thi ^ __ldg(p.pc_xhi + q);
         if (v.blk_of_khi[__popc(shi)] >= 0) break;
@@ -358,13 +366,14 @@ k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__
     }
     __syncthreads();
 
-    int q = next_piece<R, KIND>(v, p, -1, rc.thi);
+    const int pend = geo.split_p0[rc.split + 1];
+    int q = next_piece<R, KIND>(v, p, geo.split_p0[rc.split] - 1, rc.thi, pend);
     if (NBUF > 1) {
         int c = 0;
-        if (q < p.P) stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
-        while (q < p.P) {
-            const int qn = next_piece<R, KIND>(v, p, q, rc.thi);
-            if (qn < p.P) {
+        if (q < pend) stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
+        while (q < pend) {
+            const int qn = next_piece<R, KIND>(v, p, q, rc.thi, pend);
+            if (qn < pend) {
                 stage_piece<R, KIND, REALH>(v, p, qn, rc.thi, psi, c ? B0 : B1, &klo_req[c ^ 1]);
                 cp_async_wait<1>();
             } else {
@@ -377,13 +386,13 @@ k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__
             q = qn;
         }
     } else {
-        while (q < p.P) {
+        while (q < pend) {
             stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
             cp_async_wait<0>();
             __syncthreads();
             gather_piece<R, KIND, REALH, TPT>(p, q, B0, klo_req[0], tlo, accr, acci);
             __syncthreads();
-            q = next_piece<R, KIND>(v, p, q, rc.thi);
+            q = next_piece<R, KIND>(v, p, q, rc.thi, pend);
         }
     }
 
@@ -397,7 +406,8 @@ k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__
             C2 o;
             o.x = accr[j];
             o.y = acci[j];
-            out[idx] = o;
+            // split launches write partial sums to slice `split` of the scratch
+            out[(flags & 4) ? (int64_t)rc.split * v.dim + idx : idx] = o;
         }
         if (flags & 2) {
             const C2 ps = psi[idx];
@@ -435,13 +445,65 @@ k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__
 }
 
 
+// out[i] = sum_k part[k][i] in a fixed order, then (optionally) the FP64
+// expectation partial sums of pauli_expect for this block's elements.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_combine(int nsplit, int64_t dim, const typename Cx<R>::T *__restrict__ part, const typename Cx<R>::T *__restrict__ psi,
+          typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
+    using C2 = typename Cx<R>::T;
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    double er = 0.0, ei = 0.0, h2 = 0.0, p2 = 0.0;
+    if (i < dim) {
+        C2 s = part[i];
+        for (int k = 1; k < nsplit; ++k) {
+            const C2 t = part[(int64_t)k * dim + i];
+            s.x += t.x;
+            s.y += t.y;
+        }
+        if (flags & 1) out[i] = s;
+        if (flags & 2) {
+            const C2 ps = psi[i];
+            const double pr = (double)ps.x, pi = (double)ps.y, hr = (double)s.x, hi = (double)s.y;
+            er = pr * hr + pi * hi;
+            ei = pr * hi - pi * hr;
+            h2 = hr * hr + hi * hi;
+            p2 = pr * pr + pi * pi;
+        }
+    }
+    if (flags & 2) {
+        __shared__ double red[4][kThreads / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            er += __shfl_down_sync(0xffffffffu, er, o);
+            ei += __shfl_down_sync(0xffffffffu, ei, o);
+            h2 += __shfl_down_sync(0xffffffffu, h2, o);
+            p2 += __shfl_down_sync(0xffffffffu, p2, o);
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[0][warp] = er;
+            red[1][warp] = ei;
+            red[2][warp] = h2;
+            red[3][warp] = p2;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double sum = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) sum += red[threadIdx.x][w];
+            partials[(int64_t)blockIdx.x * 4 + threadIdx.x] = sum;
+        }
+    }
+}
+
 int env_int(const char *name, int dflt) {
     const char *e = std::getenv(name);
     if (!e || !*e) return dflt;
     return std::atoi(e);
 }
 
-Geom make_geom(const SectorView &v, int tile) {
+Geom make_geom(const SectorView &v, int tile, int nsplit = 1, const int32_t *split_p0 = nullptr,
+               int32_t npieces = 0) {
     Geom g;
     g.nblk = v.nblk;
     g.tile = tile;
@@ -452,6 +514,11 @@ Geom make_geom(const SectorView &v, int tile) {
         const int64_t ctas = (v.dlo[b] > 0) ? v.dhi[b] * nt : 0;
         g.cta_off[b + 1] = g.cta_off[b] + ctas;
     }
+    g.nsplit = nsplit;
+    g.split_p0[0] = 0;
+    g.split_p0[1] = npieces;
+    if (split_p0)
+        for (int k = 0; k <= nsplit; ++k) g.split_p0[k] = split_p0[k];
     return g;
 }
 
@@ -508,19 +575,32 @@ void launch_kind(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, cons
 
 template <typename R>
 void launch_apply_prec(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out,
-                       double *partials, cudaStream_t st) {
-    const Geom geo = make_geom(v, cfg.tpt * kThreads);
+                       double *partials, void *split_buf, cudaStream_t st) {
+    using C2 = typename Cx<R>::T;
+    const Geom geo = make_geom(v, cfg.tpt * kThreads, cfg.nsplit, cfg.split_p0.data(), (int32_t)p.P);
     const PlanDev pd = plan_dev(p);
-    const int flags = (out ? 1 : 0) | (partials ? 2 : 0);
     const int kind = v.kind == PAULI_SECTOR_FULL ? KFULL : (v.nblk == 1 ? KBLK1 : KBLKN);
+    void *kout = out;
+    int flags = (out ? 1 : 0) | (partials ? 2 : 0);
+    if (cfg.nsplit > 1) {
+        kout = split_buf;
+        flags = 1 | 4;
+    }
     if (p.real) {
-        if (kind == KFULL) launch_kind<R, KFULL, true>(cfg, v, geo, pd, in, out, partials, flags, st);
-        else if (kind == KBLK1) launch_kind<R, KBLK1, true>(cfg, v, geo, pd, in, out, partials, flags, st);
-        else launch_kind<R, KBLKN, true>(cfg, v, geo, pd, in, out, partials, flags, st);
+        if (kind == KFULL) launch_kind<R, KFULL, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else if (kind == KBLK1) launch_kind<R, KBLK1, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else launch_kind<R, KBLKN, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
     } else {
-        if (kind == KFULL) launch_kind<R, KFULL, false>(cfg, v, geo, pd, in, out, partials, flags, st);
-        else if (kind == KBLK1) launch_kind<R, KBLK1, false>(cfg, v, geo, pd, in, out, partials, flags, st);
-        else launch_kind<R, KBLKN, false>(cfg, v, geo, pd, in, out, partials, flags, st);
+        if (kind == KFULL) launch_kind<R, KFULL, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else if (kind == KBLK1) launch_kind<R, KBLK1, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else launch_kind<R, KBLKN, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
+    }
+    if (cfg.nsplit > 1) {
+        const int cflags = (out ? 1 : 0) | (partials ? 2 : 0);
+        k_combine<R><<<(unsigned)cfg.combine_nct, kThreads, 0, st>>>(
+            cfg.nsplit, v.dim, static_cast<const C2 *>(split_buf), static_cast<const C2 *>(in), static_cast<C2 *>(out),
+            partials, cflags);
+        PS_LAUNCH_CHECK();
     }
 }
 

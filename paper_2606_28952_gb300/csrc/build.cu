@@ -445,6 +445,7 @@ void free_plan(const Allocator &al, Plan &p) {
     dev_free(al, p.s_zlo); dev_free(al, p.s_t0);
     dev_free(al, p.t_zhi); dev_free(al, p.t_c64); dev_free(al, p.t_c32);
     dev_free(al, p.partials);
+    dev_free(al, p.split_buf);
     p = Plan();
 }
 
@@ -552,6 +553,14 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
     it_s0.push_back((int32_t)S);
     p.P = (int64_t)pc_xhi.size();
     p.I = (int64_t)it_xlo.size();
+    // work estimate of a piece for one target: staging plus, per item, the gather
+    // and one parity-add per segment
+    p.h_pc_cumw.assign(p.P + 1, 0);
+    for (int64_t q = 0; q < p.P; ++q) {
+        int64_t wq = 8;
+        for (int32_t it = pc_i0[q]; it < pc_i0[q + 1]; ++it) wq += 4 + (it_s0[it + 1] - it_s0[it]);
+        p.h_pc_cumw[q + 1] = p.h_pc_cumw[q] + wq;
+    }
     p.nseg_diag = (G > 0 && gx[0] == 0) ? g_s0[1] - g_s0[0] : 0;
     auto upload = [&](const void *src, size_t bytes) {
         void *d = dev_alloc(al, bytes > 0 ? bytes : 4);

@@ -70,7 +70,8 @@ extern "C" int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const v
         Plan *p = find_plan(H, s->v.n_lo);
         PS_CHECK(p != nullptr, PAULI_EINVAL,
                  "no apply plan for this sector split: call pauli_prepare(H, s) once before pauli_expect_noalloc");
-        const int64_t nct = apply_num_ctas(*p, s->v, dtype);
+        // one CTA per (row, column tile), no split: the launch touches no scratch but the static array
+        const int64_t nct = apply_num_ctas(*p, s->v, dtype, false);
         PS_CHECK(nct <= kNoallocMaxBlocks, PAULI_EUNSUPPORTED,
                  "pauli_expect_noalloc: this sector needs " + std::to_string(nct) +
                      " thread blocks of partial sums; the static scratch holds " + std::to_string(kNoallocMaxBlocks));
@@ -82,7 +83,7 @@ extern "C" int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const v
         double *scratch = scratch_on_current_device();
         // every block overwrites its own 4 partials before k_reduce reads them,
         // so nothing left over from an earlier call has to be cleared
-        launch_apply(H, *p, s->v, psi, hpsi_out, dtype, scratch, cs);
+        launch_apply(H, *p, s->v, psi, hpsi_out, dtype, scratch, cs, false);
         launch_reduce(scratch, nct, result, cs);
         return PAULI_OK;
     } catch (const Error &e) {

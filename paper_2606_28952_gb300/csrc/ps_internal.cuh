@@ -120,9 +120,13 @@ struct Plan {
     uint32_t *t_zhi = nullptr;         // [M] (segment order)
     double2 *t_c64 = nullptr;          // [M] FP64 coefficients
     float2 *t_c32 = nullptr;           // [M] FP32 coefficients
+    std::vector<int64_t> h_pc_cumw;   // [P+1] cumulative per-piece work estimate
     // reduction scratch for pauli_expect
     double *partials = nullptr;
     int64_t partials_cap = 0;
+    // partial vectors of split launches (bytes)
+    void *split_buf = nullptr;
+    int64_t split_cap = 0;
 };
 
 struct PlanLimits {
@@ -196,16 +200,23 @@ void sector_unrank(const SectorView &v, const int64_t *idx, int64_t n, uint64_t 
 
 // apply.cu
 struct ApplyCfg {
-    int tpt = 1;        // targets (columns) per thread
-    int nbuf = 1;       // staged source rows in flight (1 or 2)
-    size_t smem = 0;    // dynamic shared memory per CTA
-    int64_t nct = 0;    // CTAs of one launch
+    int tpt = 1;            // targets (columns) per thread
+    int nbuf = 1;           // staged source rows in flight (1 or 2)
+    size_t smem = 0;        // dynamic shared memory per CTA
+    int64_t base_nct = 0;   // (row, column tile) CTAs
+    int nsplit = 1;         // piece ranges per (row, tile)
+    std::vector<int32_t> split_p0;
+    int64_t nct = 0;        // CTAs of the gather launch = base_nct * nsplit
+    int64_t combine_nct = 0;
 };
-ApplyCfg apply_config(const SectorView &v, int dtype);
+ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split);
 void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *psi_in,
-                  void *psi_out, int dtype, double *partials, cudaStream_t st);
+                  void *psi_out, int dtype, double *partials, cudaStream_t st, bool allow_split = true);
 void launch_reduce(const double *partials, int64_t nparts, double *result, cudaStream_t st);
-int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype);
+// number of 4-double partial-sum slots an expectation launch writes
+int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow_split = true);
+// elements of the split scratch a launch needs (0: no split)
+int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype);
 void launch_rotate(pauli_sum *G, const SectorView &v, double theta, void *psi, int dtype,
                    cudaStream_t st);
 }  // namespace ps
