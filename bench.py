@@ -63,12 +63,35 @@ def count_updates(x: np.ndarray, n_lo: int, n_hi: int, k_lo: int, k_hi: int) -> 
 
 
 def measured_peaks():
+    """(HBM GB/s, kind, max SM MHz) from MEASURED_PEAKS.json, else the fallback figures."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return d.get("hbm_gbs", 6800.0), "measured"
-    return 6800.0, "fallback"
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, "fallback", 2070.0
+
+
+# Popcount results per SM per clock on sm_103a (CUDA throughput table; a probe on
+# the GB300 measured 15.8).  One term-amplitude update of eq. reverse_sum needs one
+# popcount parity, so SMs x 16 x clock is the update roof of the parity pipe.
+POPC_PER_CLK_SM = 16
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel sources
+    still match the ones captured (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    h = hashlib.sha256()
+    for s in d["sources"]:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    return d["dram_bytes_per_launch"] if h.hexdigest() == d["sources_sha256"] else None
 
 
 # ---------------------------------------------------------------------------
@@ -261,10 +284,13 @@ def run_ours(args, rank, world, local_rank):
     bytes_io = S.dim * esize
 
     # roofline bookkeeping for the apply kernel
-    hbm_peak, peak_kind = measured_peaks()
+    hbm_peak, peak_kind, sm_mhz_max = measured_peaks()
     table_bytes = H.m * (8 + 8 + 2 * (4 if args.dtype == "c64" else 8)) + H.n_groups * 16
     alg_bytes = 2 * S.dim * esize + table_bytes
     achieved_gbs = alg_bytes / t_step / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    popc_peak = sms * POPC_PER_CLK_SM * sm_mhz_max * 1e6 / 1e9  # G parities / s
+    achieved_gups = U / t_step / 1e9
 
     # side measurements (not the headline): expectation value and the other precision
     res = torch.empty(4, dtype=torch.float64, device=dev)
@@ -305,9 +331,13 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": "mol24: 24 qubits, 12 orbitals, seed 0, (6a,6b) sector D=853776",
                        "terms": H.m, "groups": H.n_groups, "updates_per_apply": U,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"},
-            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved_gbs / hbm_peak, "traffic": None,
-                         "note": f"compulsory bytes {alg_bytes} per apply; peak {peak_kind}"},
+            "roofline": {"bound": "alu", "achieved": achieved_gups, "peak": popc_peak, "unit": "Gupd/s",
+                         "frac": achieved_gups / popc_peak,
+                         "traffic": profiled_traffic("k_apply_mol24_c64.json") if args.dtype == "c64" else None,
+                         "note": (f"updates U={U} per launch / CUDA-event step time; peak = {sms} SMs x "
+                                  f"{POPC_PER_CLK_SM} popcounts/clk x {sm_mhz_max:.0f} MHz (one parity per "
+                                  f"update); HBM view: {alg_bytes} compulsory bytes -> {achieved_gbs:.2f} GB/s "
+                                  f"= {achieved_gbs / hbm_peak:.5f} of {peak_kind} {hbm_peak} GB/s")},
             "cpu_baseline": cpu,
             "e2e": {"value": world * U / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io},
