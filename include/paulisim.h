@@ -230,6 +230,35 @@ int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const void *psi, i
 int pauli_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, int dtype,
                  pauli_stream_t st);
 
+/* ------------------------------------------------------------------------- */
+/* real-time propagation by Krylov (Lanczos) projection                       */
+/* ------------------------------------------------------------------------- */
+
+/* psi <- exp(-i dt H) psi on the sector for a Hermitian H, by an m-vector
+ * Lanczos projection (the paper names Krylov solvers as users of the same
+ * operator engine, Sec. 4): v_0 = psi/||psi||, w_j = H v_j, alpha_j = <v_j|w_j>,
+ * w_j -= alpha_j v_j + beta_j v_{j-1}, beta_{j+1} = ||w_j||, v_{j+1} = w_j/beta_{j+1},
+ * psi = ||psi|| V_m exp(-i dt T_m) e_0.  Vectors are stored in dtype; alpha,
+ * beta and the m x m exponential (cyclic Jacobi eigen-decomposition of T_m)
+ * are FP64 and stay on the device.  2 <= m <= 32.  The handle owns
+ * (m+1) x dim vectors of scratch (pauli_krylov_create allocates them and
+ * calls pauli_prepare).  A zero w_j (invariant subspace) gives zero later
+ * vectors and an exact result. */
+typedef struct pauli_krylov pauli_krylov;
+int pauli_krylov_create(pauli_sum *H, const pauli_sector *s, int m, int dtype, pauli_krylov **out);
+
+/* nsteps propagation steps of length dt on st.  use_graph != 0: the step is
+ * captured once as a CUDA graph (after one eager step, re-captured when psi,
+ * dt or st change) and replayed, so a step makes no host round trip. */
+int pauli_krylov_step(pauli_krylov *k, void *psi, double dt, int nsteps, int use_graph,
+                      pauli_stream_t st);
+
+/* Copies the last step's alpha[m] and beta[m+1] (beta[0] = ||psi||) to host
+ * arrays; synchronizes st. */
+int pauli_krylov_scalars(const pauli_krylov *k, double *alpha, double *beta, pauli_stream_t st);
+
+int pauli_krylov_destroy(pauli_krylov *k);
+
 /* Reads and clears H's device status word; synchronizes st.  *code is
  * PAULI_OK or the first device-side error recorded since the last read. */
 int pauli_status(pauli_sum *H, pauli_stream_t st, int *code);

@@ -66,6 +66,18 @@ def pauli_sum_matrix(n: int, x, z, c, sparse: bool = False):
     return H if sparse else H.toarray()
 
 
+def sector_matrix(n: int, x, z, c, configs) -> np.ndarray:
+    """Dense H restricted to the rows and columns of the given configurations."""
+    idx = np.asarray(configs, dtype=np.int64)
+    return pauli_sum_matrix(n, x, z, c, sparse=True)[idx][:, idx].toarray()
+
+
+def propagate(Hs: np.ndarray, psi: np.ndarray, t: float) -> np.ndarray:
+    """exp(-i t H) psi for a Hermitian dense matrix by its eigen-decomposition (numpy eigh)."""
+    lam, V = np.linalg.eigh(Hs)
+    return V @ (np.exp(-1j * t * lam) * (V.conj().T @ psi))
+
+
 def annihilator(n_modes: int, P: int):
     """a_P on occupation-number states |b>, bit Q of b = occupation of mode Q:
     a_P |b> = (-1)^(sum_{Q<P} b_Q) |b - e_P> if b_P = 1, else 0  (sparse CSR)."""

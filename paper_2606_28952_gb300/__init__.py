@@ -59,6 +59,10 @@ SIGNATURES = {
     "pauli_expect_noalloc": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "pauli_rotate": (_i32, [_vp, _vp, _dbl, _vp, _i32, _vp]),
     "pauli_status": (_i32, [_vp, _vp, _vp]),
+    "pauli_krylov_create": (_i32, [_vp, _vp, _i32, _i32, _vp]),
+    "pauli_krylov_step": (_i32, [_vp, _vp, _dbl, _i32, _i32, _vp]),
+    "pauli_krylov_scalars": (_i32, [_vp, _vp, _vp, _vp]),
+    "pauli_krylov_destroy": (_i32, [_vp]),
 }
 
 
@@ -330,6 +334,43 @@ def expect_noalloc(H: PauliSum, s: Sector, psi, result, hpsi_out=None, stream=No
     _check(lib().pauli_expect_noalloc(H._h, s._h, C.c_void_p(psi.data_ptr()), _dtype_code(psi),
                                       C.c_void_p(result.data_ptr()), hp, _stream_ptr(stream)))
     return result
+
+
+class Krylov:
+    """m-vector Lanczos propagator psi <- exp(-i dt H) psi (device scalars, optional CUDA graph)."""
+
+    def __init__(self, H: PauliSum, s: Sector, m: int = 20, dtype=None):
+        import torch
+        code = C64 if dtype in (None, torch.complex64) else C128
+        out = C.c_void_p()
+        _check(lib().pauli_krylov_create(H._h, s._h, m, code, C.byref(out)))
+        self._h, self.H, self.s, self.m, self.code = out, H, s, m, code
+
+    def step(self, psi, dt: float, nsteps: int = 1, graph: bool = True, stream=None):
+        _check_state(psi, self.s.dim, "psi")
+        if _dtype_code(psi) != self.code:
+            raise TypeError("psi dtype does not match the propagator")
+        _check(lib().pauli_krylov_step(self._h, C.c_void_p(psi.data_ptr()), float(dt), int(nsteps), int(graph),
+                                       _stream_ptr(stream)))
+        return psi
+
+    def scalars(self, stream=None):
+        a = np.zeros(self.m)
+        b = np.zeros(self.m + 1)
+        _check(lib().pauli_krylov_scalars(self._h, _np_ptr(a), _np_ptr(b), _stream_ptr(stream)))
+        return a, b
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            if _lib is not None:
+                lib().pauli_krylov_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rotate(G: PauliSum, s: Sector, theta: float, psi, stream=None):
