@@ -148,6 +148,20 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     c.nbuf = nbuf;
     c.smem = nbuf * bb;
     c.base_nct = make_geom(v, tpt * kThreads).cta_off[v.nblk];
+    // small operators (lattice models): the whole folded plan fits in shared
+    // memory and rows have few pieces, so gather straight from global memory
+    c.direct = env_int("PAULISIM_DIRECT", (p.I <= kDirectItems && p.S <= kDirectSegs) ? 1 : 0) != 0 &&
+               p.I <= kDirectItems && p.S <= kDirectSegs;
+    if (c.direct) {
+        c.smem = 0;
+        c.nbuf = 1;
+        c.nsplit = 1;
+        c.split_p0.assign(2, 0);
+        c.split_p0[1] = (int32_t)p.P;
+        c.nct = c.base_nct;
+        c.combine_nct = 0;
+        return c;
+    }
     // Too few rows for the GPU: split each row's pieces into nsplit balanced
     // ranges (by the plan's per-piece work estimate) so that a launch has about
     // four waves of CTAs; k_combine adds the partial vectors in a fixed order.

@@ -64,9 +64,13 @@ struct PlanDev {
     const uint32_t *pc_xhi;
     const int32_t *pc_i0;
     const uint32_t *it_xlo;
+    const uint32_t *it_xhi;
     const int32_t *it_s0;
+    int32_t I;
     const uint32_t *s_zlo;
+    const uint32_t *s_xhi;
     const int32_t *s_t0;
+    int32_t S;
     const uint32_t *t_zhi;
     const double2 *t_c64;
     const float2 *t_c32;
@@ -445,6 +449,232 @@ k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__
 }
 
 
+// ---------------------------------------------------------------------------
+// Direct variant for small operators (few groups per row, e.g. lattice models):
+// the whole plan, folded for this CTA's row, lives in shared memory and every
+// source amplitude is read straight from global memory (coalesced along a row
+// of the full space), so a row costs one barrier instead of one per piece.
+// ---------------------------------------------------------------------------
+constexpr int kDirectItems = 256;
+constexpr int kDirectSegs = 1024;
+
+struct DItem {
+    int64_t base;   // index of column 0 of the source row
+    uint32_t xlo;
+    int klo;        // popcount required of the source column, -1: row invalid
+    int s0, s1;     // segment range (the first is skipped into f0 when its z_lo == 0)
+    int diag;       // x = 0 group on the FP32 path: compensated sum
+    int pad;
+};
+
+template <typename R, int KIND, bool REALH, int TPT>
+__global__ void __launch_bounds__(kThreads)
+k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
+               typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
+    using C2 = typename Cx<R>::T;
+    __shared__ DItem sm_it[kDirectItems];
+    __shared__ uint32_t sm_z[kDirectSegs];
+    __shared__ C2 sm_a[kDirectSegs];
+    __shared__ float2 sm_lo[kDirectSegs];
+    const RowCtx rc = decode_row<KIND == KFULL>(v, geo);
+    const int tid = threadIdx.x;
+    // phase 1a: the source row of every item for this CTA's row
+    for (int it = tid; it < p.I; it += kThreads) {
+        const uint32_t shi = rc.thi ^ __ldg(p.it_xhi + it);
+        const int s0 = __ldg(p.it_s0 + it), s1 = __ldg(p.it_s0 + it + 1);
+        DItem e;
+        e.xlo = __ldg(p.it_xlo + it);
+        e.s0 = s0;
+        e.s1 = s1;
+        e.diag = (sizeof(R) == 4 && s0 < p.nseg_diag) ? 1 : 0;
+        e.pad = 0;
+        if (KIND == KFULL) {
+            e.klo = 0;
+            e.base = (int64_t)shi << v.n_lo;
+        } else {
+            const int bb = v.blk_of_khi[__popc(shi)];
+            e.klo = bb < 0 ? -1 : v.klo[bb];
+            e.base = bb < 0 ? 0 : v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
+        }
+        sm_it[it] = e;
+    }
+    // phase 1b: one thread per segment folds the row's high-half phases
+    for (int s = tid; s < p.S; s += kThreads) {
+        const uint32_t shi = rc.thi ^ __ldg(p.s_xhi + s);
+        const int t0 = __ldg(p.s_t0 + s), t1 = __ldg(p.s_t0 + s + 1);
+        C2 a;
+        float2 lo = make_float2(0.f, 0.f);
+        if (sizeof(R) == 4 && s < p.nseg_diag) {
+            double ar = 0.0, ai = 0.0;
+            for (int t = t0; t < t1; ++t) {
+                const double2 c = __ldg(p.t_c64 + t);
+                const uint32_t par = __popc(__ldg(p.t_zhi + t) & shi);
+                ar += flip(c.x, par);
+                ai += flip(c.y, par);
+            }
+            a.x = (R)ar;
+            a.y = (R)ai;
+            lo = make_float2((float)(ar - (double)(float)ar), (float)(ai - (double)(float)ai));
+        } else {
+            R ar = R(0), ai = R(0);
+            for (int t = t0; t < t1; ++t) {
+                const C2 c = coef<R>(p, t);
+                const uint32_t par = __popc(__ldg(p.t_zhi + t) & shi);
+                ar += flip(c.x, par);
+                if (!REALH) ai += flip(c.y, par);
+            }
+            a.x = ar;
+            a.y = ai;
+        }
+        sm_a[s] = a;
+        sm_lo[s] = lo;
+        sm_z[s] = __ldg(p.s_zlo + s);
+    }
+    uint32_t tlo[TPT];
+    bool act[TPT];
+    R accr[TPT], acci[TPT];
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) {
+        const int64_t c = rc.c0 + tid + j * kThreads;
+        act[j] = c < rc.dlo;
+        tlo[j] = 0;
+        if (act[j]) tlo[j] = (KIND == KFULL) ? (uint32_t)c : __ldg(v.list_lo + v.list_lo_off[v.klo[rc.blk]] + c);
+        accr[j] = R(0);
+        acci[j] = R(0);
+    }
+    __syncthreads();
+    // phase 2: gather from global memory
+    for (int it = 0; it < p.I; ++it) {
+        const DItem e = sm_it[it];
+        if (e.klo < 0) continue;
+        uint32_t s[TPT];
+        C2 amp[TPT];
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            s[j] = tlo[j] ^ e.xlo;
+            int64_t idx;
+            bool ok = act[j];
+            if (KIND == KFULL) {
+                idx = e.base + s[j];
+            } else {
+                ok = ok && (__popc(s[j]) == e.klo);
+                idx = e.base + (ok ? (int64_t)__ldg(v.rank_lo + s[j]) : 0);
+            }
+            amp[j] = psi[idx];
+            if (!ok) {
+                amp[j].x = R(0);
+                amp[j].y = R(0);
+            }
+        }
+        R fr[TPT], fi[TPT];
+        int sg = e.s0;
+        const bool zfirst = sm_z[e.s0] == 0;
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            fr[j] = zfirst ? sm_a[e.s0].x : R(0);
+            fi[j] = zfirst ? sm_a[e.s0].y : R(0);
+        }
+        if (zfirst) ++sg;
+        if (sizeof(R) == 4 && e.diag) {
+            R er[TPT], ei[TPT];
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                er[j] = zfirst ? (R)sm_lo[e.s0].x : R(0);
+                ei[j] = zfirst ? (R)sm_lo[e.s0].y : R(0);
+            }
+            for (; sg < e.s1; ++sg) {
+                const uint32_t z = sm_z[sg];
+                const C2 a = sm_a[sg];
+                const float2 l = sm_lo[sg];
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) {
+                    const uint32_t par = __popc(z & s[j]);
+                    float t, err;
+                    two_sum(fr[j], flip((float)a.x, par), t, err);
+                    fr[j] = t;
+                    er[j] += err + flip(l.x, par);
+                    if (!REALH) {
+                        two_sum(fi[j], flip((float)a.y, par), t, err);
+                        fi[j] = t;
+                        ei[j] += err + flip(l.y, par);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                fr[j] += er[j];
+                fi[j] += ei[j];
+            }
+        } else {
+            for (; sg < e.s1; ++sg) {
+                const uint32_t z = sm_z[sg];
+                const C2 a = sm_a[sg];
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) {
+                    const uint32_t par = __popc(z & s[j]);
+                    fr[j] += flip(a.x, par);
+                    if (!REALH) fi[j] += flip(a.y, par);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            if (REALH) {
+                accr[j] += fr[j] * amp[j].x;
+                acci[j] += fr[j] * amp[j].y;
+            } else {
+                accr[j] += fr[j] * amp[j].x - fi[j] * amp[j].y;
+                acci[j] += fr[j] * amp[j].y + fi[j] * amp[j].x;
+            }
+        }
+    }
+    // epilogue (same contract as k_apply)
+    double er = 0.0, ei = 0.0, h2 = 0.0, p2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) {
+        if (!act[j]) continue;
+        const int64_t idx = rc.own_base + rc.c0 + tid + j * kThreads;
+        if (flags & 1) {
+            C2 o;
+            o.x = accr[j];
+            o.y = acci[j];
+            out[idx] = o;
+        }
+        if (flags & 2) {
+            const C2 ps = psi[idx];
+            const double pr = (double)ps.x, pi = (double)ps.y;
+            const double hr = (double)accr[j], hi = (double)acci[j];
+            er += pr * hr + pi * hi;
+            ei += pr * hi - pi * hr;
+            h2 += hr * hr + hi * hi;
+            p2 += pr * pr + pi * pi;
+        }
+    }
+    if (flags & 2) {
+        __shared__ double red[4][kThreads / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            er += __shfl_down_sync(0xffffffffu, er, o);
+            ei += __shfl_down_sync(0xffffffffu, ei, o);
+            h2 += __shfl_down_sync(0xffffffffu, h2, o);
+            p2 += __shfl_down_sync(0xffffffffu, p2, o);
+        }
+        const int lane = tid & 31, warp = tid >> 5;
+        if (lane == 0) {
+            red[0][warp] = er;
+            red[1][warp] = ei;
+            red[2][warp] = h2;
+            red[3][warp] = p2;
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double sum = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) sum += red[tid][w];
+            partials[(int64_t)blockIdx.x * 4 + tid] = sum;
+        }
+    }
+}
+
 // out[i] = sum_k part[k][i] in a fixed order, then (optionally) the FP64
 // expectation partial sums of pauli_expect for this block's elements.
 template <typename R>
@@ -529,9 +759,13 @@ PlanDev plan_dev(const Plan &p) {
     d.pc_xhi = p.pc_xhi;
     d.pc_i0 = p.pc_i0;
     d.it_xlo = p.it_xlo;
+    d.it_xhi = p.it_xhi;
     d.it_s0 = p.it_s0;
+    d.I = (int32_t)p.I;
     d.s_zlo = p.s_zlo;
+    d.s_xhi = p.s_xhi;
     d.s_t0 = p.s_t0;
+    d.S = (int32_t)p.S;
     d.t_zhi = p.t_zhi;
     d.t_c64 = p.t_c64;
     d.t_c32 = p.t_c32;
@@ -556,6 +790,19 @@ void launch_one(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, const
 template <typename R, int KIND, bool REALH>
 void launch_kind(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, const PlanDev &pd, const void *in,
                  void *out, double *partials, int flags, cudaStream_t st) {
+    if (cfg.direct) {
+        using C2 = typename Cx<R>::T;
+        const C2 *pin = static_cast<const C2 *>(in);
+        C2 *pout = static_cast<C2 *>(out);
+        const unsigned g = (unsigned)cfg.nct;
+        switch (cfg.tpt) {
+            case 4: k_apply_direct<R, KIND, REALH, 4><<<g, kThreads, 0, st>>>(v, geo, pd, pin, pout, partials, flags); break;
+            case 2: k_apply_direct<R, KIND, REALH, 2><<<g, kThreads, 0, st>>>(v, geo, pd, pin, pout, partials, flags); break;
+            default: k_apply_direct<R, KIND, REALH, 1><<<g, kThreads, 0, st>>>(v, geo, pd, pin, pout, partials, flags); break;
+        }
+        PS_LAUNCH_CHECK();
+        return;
+    }
 #define PS_L(T, N) launch_one<R, KIND, REALH, T, N>(cfg, v, geo, pd, in, out, partials, flags, st)
     if (cfg.nbuf == 2) {
         switch (cfg.tpt) {

@@ -442,6 +442,8 @@ void jw_fermion_raw_device(int n, int nterms, const int *nf, const int *modes, c
 
 void free_plan(const Allocator &al, Plan &p) {
     dev_free(al, p.pc_xhi); dev_free(al, p.pc_i0); dev_free(al, p.it_xlo); dev_free(al, p.it_s0);
+    dev_free(al, p.it_xhi);
+    dev_free(al, p.s_xhi);
     dev_free(al, p.s_zlo); dev_free(al, p.s_t0);
     dev_free(al, p.t_zhi); dev_free(al, p.t_c64); dev_free(al, p.t_c32);
     dev_free(al, p.partials);
@@ -524,7 +526,7 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
     if (G > 0) PS_CUDA(cudaMemcpy(gx.data(), h->gx, G * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     const uint64_t lomask = (n_lo >= 64) ? ~0ull : ((1ull << n_lo) - 1ull);
     // pieces of consecutive groups with one x_hi; items of at most kSegsPerPiece segments
-    std::vector<uint32_t> pc_xhi, it_xlo;
+    std::vector<uint32_t> pc_xhi, it_xlo, it_xhi;
     std::vector<int32_t> pc_i0, it_s0;
     int items_in_piece = 0, segs_in_piece = 0;
     uint64_t cur_xhi = ~0ull;
@@ -543,6 +545,7 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
                 segs_in_piece = 0;
             }
             it_xlo.push_back((uint32_t)xlo);
+            it_xhi.push_back((uint32_t)xhi);
             it_s0.push_back(s);
             ++items_in_piece;
             segs_in_piece += take;
@@ -570,6 +573,13 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
     p.pc_xhi = static_cast<uint32_t *>(upload(pc_xhi.data(), pc_xhi.size() * sizeof(uint32_t)));
     p.pc_i0 = static_cast<int32_t *>(upload(pc_i0.data(), pc_i0.size() * sizeof(int32_t)));
     p.it_xlo = static_cast<uint32_t *>(upload(it_xlo.data(), it_xlo.size() * sizeof(uint32_t)));
+    p.it_xhi = static_cast<uint32_t *>(upload(it_xhi.data(), it_xhi.size() * sizeof(uint32_t)));
+    {
+        std::vector<uint32_t> s_xhi(S > 0 ? S : 1, 0);
+        for (size_t it = 0; it < it_xhi.size(); ++it)
+            for (int32_t s = it_s0[it]; s < it_s0[it + 1]; ++s) s_xhi[s] = it_xhi[it];
+        p.s_xhi = static_cast<uint32_t *>(upload(s_xhi.data(), (S > 0 ? S : 0) * sizeof(uint32_t)));
+    }
     p.it_s0 = static_cast<int32_t *>(upload(it_s0.data(), it_s0.size() * sizeof(int32_t)));
     h->plans[h->nplans] = p;
     return h->plans[h->nplans++];

@@ -114,8 +114,10 @@ struct Plan {
     uint32_t *pc_xhi = nullptr;        // [P]
     int32_t *pc_i0 = nullptr;          // [P+1] item range
     uint32_t *it_xlo = nullptr;        // [I]
+    uint32_t *it_xhi = nullptr;        // [I] x_hi of the item's group
     int32_t *it_s0 = nullptr;          // [I+1] segment range
     uint32_t *s_zlo = nullptr;         // [S]
+    uint32_t *s_xhi = nullptr;         // [S] x_hi of the segment's group
     int32_t *s_t0 = nullptr;           // [S+1] term range
     uint32_t *t_zhi = nullptr;         // [M] (segment order)
     double2 *t_c64 = nullptr;          // [M] FP64 coefficients
@@ -208,6 +210,7 @@ struct ApplyCfg {
     std::vector<int32_t> split_p0;
     int64_t nct = 0;        // CTAs of the gather launch = base_nct * nsplit
     int64_t combine_nct = 0;
+    bool direct = false;    // small plan: k_apply_direct (no staging, no split)
 };
 ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split);
 void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *psi_in,
