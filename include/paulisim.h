@@ -231,6 +231,65 @@ int pauli_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, i
                  pauli_stream_t st);
 
 /* ------------------------------------------------------------------------- */
+/* launch-shape autotuning                                                    */
+/* ------------------------------------------------------------------------- */
+
+/* Launch shape of pauli_apply / pauli_expect for one (operator, sector, dtype):
+ * columns (targets) per thread, staged source rows in flight, piece ranges a
+ * row is split into (their partial vectors are added in a fixed order), and
+ * direct gather (operators small enough to keep whole in shared memory) vs
+ * staged source rows.  ms: measured time of one apply (0 if not measured). */
+typedef struct {
+    int cols_per_thread;  /* 1, 2 or 4 */
+    int staged_rows;      /* 1 or 2 */
+    int row_split;        /* 1..16 */
+    int direct;           /* 0 or 1 */
+    double ms;
+} pauli_launch_config;
+
+/* Times every realisable shape (reps launches each, CUDA events on st, after
+ * one warm-up launch, on scratch vectors the call allocates) and keeps the
+ * fastest in H for this sector and dtype; later applies use it.  Blocking. */
+int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_launch_config *best,
+               pauli_stream_t st);
+
+/* Installs a shape (e.g. read back from a cache of earlier pauli_tune results). */
+int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, const pauli_launch_config *cfg);
+
+/* The shape pauli_apply currently uses for this sector and dtype (needs a plan). */
+int pauli_get_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, pauli_launch_config *cfg);
+
+/* ------------------------------------------------------------------------- */
+/* many independent states in one persistent launch                           */
+/* ------------------------------------------------------------------------- */
+
+/* A batch of n (operator, sector) pairs -- e.g. the points of a scan or the
+ * parameter-shifted states of a gradient -- applied together: one grid of
+ * resident CTAs pulls (state, row, column tile) work units from an atomic
+ * queue, largest states first, so states of very different sizes share the
+ * GPU in one launch.  Every sector must be a single product block; the
+ * handles must outlive the batch; pauli_batch_create calls pauli_prepare on
+ * each pair. */
+typedef struct pauli_batch pauli_batch;
+int pauli_batch_create(int n, pauli_sum *const *H, const pauli_sector *const *S, int dtype,
+                       pauli_batch **out);
+
+/* For every state b: psi_out[b] = H_b psi_in[b] (skipped if psi_out is NULL
+ * or psi_out[b] is NULL) and, if results is not NULL, results[4b..4b+3] =
+ * { Re <psi|H|psi>, Im <psi|H|psi>, ||H psi||^2, <psi|psi> } (DEVICE array,
+ * FP64, fixed reduction order).  psi_in / psi_out are HOST arrays of n device
+ * pointers.  The only atomic is the work-queue counter. */
+int pauli_batch_apply(pauli_batch *b, const void *const *psi_in, void *const *psi_out, double *results,
+                      pauli_stream_t st);
+
+/* Times the batched launch for every columns-per-thread / staged-rows shape on
+ * the given vectors and keeps the fastest.  Blocking. */
+int pauli_batch_tune(pauli_batch *b, const void *const *psi_in, void *const *psi_out, int reps,
+                     pauli_launch_config *best, pauli_stream_t st);
+
+int pauli_batch_destroy(pauli_batch *b);
+
+/* ------------------------------------------------------------------------- */
 /* real-time propagation by Krylov (Lanczos) projection                       */
 /* ------------------------------------------------------------------------- */
 

@@ -59,6 +59,13 @@ SIGNATURES = {
     "pauli_expect_noalloc": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "pauli_rotate": (_i32, [_vp, _vp, _dbl, _vp, _i32, _vp]),
     "pauli_status": (_i32, [_vp, _vp, _vp]),
+    "pauli_tune": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp]),
+    "pauli_set_launch_config": (_i32, [_vp, _vp, _i32, _vp]),
+    "pauli_get_launch_config": (_i32, [_vp, _vp, _i32, _vp]),
+    "pauli_batch_create": (_i32, [_i32, _vp, _vp, _i32, _vp]),
+    "pauli_batch_apply": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "pauli_batch_tune": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "pauli_batch_destroy": (_i32, [_vp]),
     "pauli_krylov_create": (_i32, [_vp, _vp, _i32, _i32, _vp]),
     "pauli_krylov_step": (_i32, [_vp, _vp, _dbl, _i32, _i32, _vp]),
     "pauli_krylov_scalars": (_i32, [_vp, _vp, _vp, _vp]),
@@ -334,6 +341,116 @@ def expect_noalloc(H: PauliSum, s: Sector, psi, result, hpsi_out=None, stream=No
     _check(lib().pauli_expect_noalloc(H._h, s._h, C.c_void_p(psi.data_ptr()), _dtype_code(psi),
                                       C.c_void_p(result.data_ptr()), hp, _stream_ptr(stream)))
     return result
+
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("cols_per_thread", C.c_int), ("staged_rows", C.c_int), ("row_split", C.c_int),
+                ("direct", C.c_int), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _tune_key(H: PauliSum, s: Sector, code: int) -> str:
+    import hashlib
+    import torch
+    n, m, g = H.info()
+    x, z, c = H.export()
+    fp = hashlib.sha256(x.tobytes() + z.tobytes() + c.tobytes()).hexdigest()[:16]
+    return (f"{torch.cuda.get_device_name()}|n{n}|lo{s.n_lo}|k{s.kind}|b{s.blocks}|d{s.dim}|M{m}|G{g}|"
+            f"{'c64' if code == C64 else 'c128'}|{fp}")
+
+
+def tune(H: PauliSum, s: Sector, dtype=None, reps: int = 5, cache: str | None = None, stream=None) -> dict:
+    """Pick the fastest launch shape for (H, s, dtype) by timing the candidates
+    (pauli_tune), or install it from a JSON cache of earlier results."""
+    import json
+    import torch
+    code = C64 if dtype in (None, torch.complex64) else C128
+    key = _tune_key(H, s, code)
+    db = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            db = json.load(f)
+    if key in db:
+        cfg = LaunchConfig(**db[key])
+        _check(lib().pauli_set_launch_config(H._h, s._h, code, C.byref(cfg)))
+        return dict(db[key], cached=True)
+    cfg = LaunchConfig()
+    _check(lib().pauli_tune(H._h, s._h, code, reps, C.byref(cfg), _stream_ptr(stream)))
+    out = cfg.as_dict()
+    if cache:
+        db[key] = out
+        tmp = cache + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return dict(out, cached=False)
+
+
+def launch_config(H: PauliSum, s: Sector, dtype=None) -> dict:
+    import torch
+    code = C64 if dtype in (None, torch.complex64) else C128
+    cfg = LaunchConfig()
+    _check(lib().pauli_get_launch_config(H._h, s._h, code, C.byref(cfg)))
+    return cfg.as_dict()
+
+
+class Batch:
+    """Many (H_b, sector_b) pairs applied in one persistent launch."""
+
+    def __init__(self, Hs, sectors, dtype=None):
+        import torch
+        self.code = C64 if dtype in (None, torch.complex64) else C128
+        self.Hs, self.sectors = list(Hs), list(sectors)
+        n = len(self.Hs)
+        harr = (C.c_void_p * n)(*[h._h.value for h in self.Hs])
+        sarr = (C.c_void_p * n)(*[s._h.value for s in self.sectors])
+        out = C.c_void_p()
+        _check(lib().pauli_batch_create(n, harr, sarr, self.code, C.byref(out)))
+        self._h = out
+
+    def _ptrs(self, tensors, name, allow_none=False):
+        n = len(self.Hs)
+        if tensors is None:
+            return None
+        vals = []
+        for t, s in zip(tensors, self.sectors):
+            if t is None and allow_none:
+                vals.append(None)
+                continue
+            _check_state(t, s.dim, name)
+            if _dtype_code(t) != self.code:
+                raise TypeError(f"{name}: dtype does not match the batch")
+            vals.append(t.data_ptr())
+        return (C.c_void_p * n)(*vals)
+
+    def apply(self, psis, outs=None, results=None, stream=None):
+        """outs[b] = H_b psis[b]; results (device float64 [n, 4]) = per-state expectation data."""
+        import torch
+        if results is None:
+            results = torch.empty((len(self.Hs), 4), dtype=torch.float64, device=psis[0].device)
+        _check(lib().pauli_batch_apply(self._h, self._ptrs(psis, "psi_in"), self._ptrs(outs, "psi_out", True),
+                                       C.c_void_p(results.data_ptr()), _stream_ptr(stream)))
+        return results
+
+    def tune(self, psis, outs=None, reps: int = 3, stream=None):
+        cfg = LaunchConfig()
+        _check(lib().pauli_batch_tune(self._h, self._ptrs(psis, "psi_in"), self._ptrs(outs, "psi_out", True), reps,
+                                      C.byref(cfg), _stream_ptr(stream)))
+        return cfg.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            if _lib is not None:
+                lib().pauli_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Krylov:

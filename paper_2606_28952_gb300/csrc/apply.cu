@@ -130,18 +130,29 @@ int num_sms() {
     return sms;
 }
 
-ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split) {
+const LaunchChoice *find_tuned(const Plan &p, const SectorView &v, int dtype) {
+    for (const TunedEntry &t : p.tuned)
+        if (t.dim == v.dim && t.nblk == v.nblk && t.dtype == dtype) return &t.choice;
+    return nullptr;
+}
+
+// Launch shape of one apply.  Each field is resolved from, in order: the
+// forced choice (the autotuner's candidate), the plan's tuned entry for this
+// sector and dtype, the PAULISIM_* environment overrides, the heuristics.
+ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split, const LaunchChoice *force) {
     ApplyCfg c;
+    LaunchChoice ch;
+    if (force) ch = *force;
+    else if (const LaunchChoice *t = find_tuned(p, v, dtype)) ch = *t;
     const int rw = 1 << v.n_lo;
     const size_t bb = dtype == PAULI_C64 ? Smem<float>::buf_bytes(rw) : Smem<double>::buf_bytes(rw);
     int64_t mx = 0;
     for (int b = 0; b < v.nblk; ++b) mx = std::max(mx, v.dlo[b]);
     // measured on the 24-qubit molecule (D_lo = 924): 4 columns per thread and a
     // single staged row (more resident CTAs) beat finer tiles and double buffering
-    int tpt = mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1);
-    tpt = env_int("PAULISIM_TPT", tpt);
+    int tpt = ch.tpt ? ch.tpt : env_int("PAULISIM_TPT", mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1));
     if (tpt != 1 && tpt != 2 && tpt != 4) tpt = 1;
-    int nbuf = env_int("PAULISIM_NBUF", 1);
+    int nbuf = ch.nbuf ? ch.nbuf : env_int("PAULISIM_NBUF", 1);
     if (nbuf != 1 && nbuf != 2) nbuf = 1;
     if (nbuf * bb > kMaxDynSmem) nbuf = 1;
     c.tpt = tpt;
@@ -150,8 +161,9 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     c.base_nct = make_geom(v, tpt * kThreads).cta_off[v.nblk];
     // small operators (lattice models): the whole folded plan fits in shared
     // memory and rows have few pieces, so gather straight from global memory
-    c.direct = env_int("PAULISIM_DIRECT", (p.I <= kDirectItems && p.S <= kDirectSegs) ? 1 : 0) != 0 &&
-               p.I <= kDirectItems && p.S <= kDirectSegs;
+    const bool fits = p.I <= kDirectItems && p.S <= kDirectSegs;
+    const int dflt_direct = env_int("PAULISIM_DIRECT", fits ? 1 : 0);
+    c.direct = fits && (ch.direct >= 0 ? ch.direct != 0 : dflt_direct != 0);
     if (c.direct) {
         c.smem = 0;
         c.nbuf = 1;
@@ -170,7 +182,7 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
         const int per_sm = std::max<int>(1, std::min<int>(2048 / kThreads, (int)((228 * 1024) / (c.smem + 2048))));
         const int64_t slots = (int64_t)num_sms() * per_sm;
         if (c.base_nct < 4 * slots) nsplit = (int)((4 * slots + c.base_nct - 1) / c.base_nct);
-        nsplit = env_int("PAULISIM_SPLIT", nsplit);
+        nsplit = ch.nsplit ? ch.nsplit : env_int("PAULISIM_SPLIT", nsplit);
         nsplit = std::max(1, std::min<int>({nsplit, kMaxSplit, (int)std::max<int64_t>(1, p.P / 8)}));
     }
     c.nsplit = nsplit;
@@ -187,20 +199,20 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     return c;
 }
 
-int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow_split) {
-    const ApplyCfg c = apply_config(p, v, dtype, allow_split);
+int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow_split, const LaunchChoice *force) {
+    const ApplyCfg c = apply_config(p, v, dtype, allow_split, force);
     return c.nsplit > 1 ? c.combine_nct : c.base_nct;
 }
 
-int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype) {
-    const ApplyCfg c = apply_config(p, v, dtype, true);
+int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype, const LaunchChoice *force) {
+    const ApplyCfg c = apply_config(p, v, dtype, true, force);
     return c.nsplit > 1 ? (int64_t)c.nsplit * v.dim : 0;
 }
 
 void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *psi_in, void *psi_out,
-                  int dtype, double *partials, cudaStream_t st, bool allow_split) {
+                  int dtype, double *partials, cudaStream_t st, bool allow_split, const LaunchChoice *force) {
     (void)H;
-    const ApplyCfg cfg = apply_config(p, v, dtype, allow_split);
+    const ApplyCfg cfg = apply_config(p, v, dtype, allow_split, force);
     if (cfg.nct == 0) return;
     PS_CHECK(cfg.nct < (1ll << 31), PAULI_EUNSUPPORTED, "apply: too many thread blocks");
     PS_CHECK(cfg.smem <= kMaxDynSmem, PAULI_EUNSUPPORTED,

@@ -91,10 +91,11 @@ struct RowCtx {
 };
 
 template <bool FULL>
-__device__ __forceinline__ RowCtx decode_row(const SectorView &v, const Geom &geo) {
+__device__ __forceinline__ RowCtx decode_row(const SectorView &v, const Geom &geo, int64_t work = -1) {
     RowCtx rc;
-    const int64_t cta = (int64_t)blockIdx.x / geo.nsplit;
-    rc.split = (int)((int64_t)blockIdx.x - cta * geo.nsplit);
+    if (work < 0) work = blockIdx.x;
+    const int64_t cta = work / geo.nsplit;
+    rc.split = (int)(work - cta * geo.nsplit);
     int b = 0;
     while (b + 1 < geo.nblk && geo.cta_off[b + 1] <= cta) ++b;
     const int64_t local = cta - geo.cta_off[b];
@@ -333,17 +334,20 @@ __device__ __forceinline__ void gather_piece(const PlanDev &p, int q, const Buf<
     }
 }
 
+// One (row, column tile, piece range) work unit of the staged gather; the body
+// of k_apply and of the persistent batched launch.  part4: this unit's 4 FP64
+// expectation partials (flags & 2).
 template <typename R, int KIND, bool REALH, int TPT, int NBUF>
-__global__ void __launch_bounds__(kThreads)
-k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
-        typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
+__device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo, const PlanDev &p, int64_t work,
+                                           const typename Cx<R>::T *__restrict__ psi,
+                                           typename Cx<R>::T *__restrict__ out, double *__restrict__ part4,
+                                           int flags, char *smem) {
     using C2 = typename Cx<R>::T;
-    extern __shared__ __align__(16) char smem[];
     __shared__ int klo_req[2];
     const int rw = 1 << v.n_lo;
     const size_t bb = Smem<R>::buf_bytes(rw);
     Buf<R> B0(smem, rw), B1(smem + (NBUF > 1 ? bb : 0), rw);
-    const RowCtx rc = decode_row<KIND == KFULL>(v, geo);
+    const RowCtx rc = decode_row<KIND == KFULL>(v, geo, work);
     const int tid = threadIdx.x;
 
     if (KIND != KFULL) {
@@ -443,9 +447,87 @@ k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__
         if (tid < 4) {
             double sum = 0.0;
             for (int w = 0; w < kThreads / 32; ++w) sum += red[tid][w];
-            partials[(int64_t)blockIdx.x * 4 + tid] = sum;
+            part4[tid] = sum;
         }
     }
+}
+
+template <typename R, int KIND, bool REALH, int TPT, int NBUF>
+__global__ void __launch_bounds__(kThreads)
+k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
+        typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
+    extern __shared__ __align__(16) char smem[];
+    apply_unit<R, KIND, REALH, TPT, NBUF>(v, geo, p, blockIdx.x, psi, out,
+                                          partials ? partials + (int64_t)blockIdx.x * 4 : nullptr, flags, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched launch: one grid of (#SM x resident) CTAs pulls work
+// units -- (state, row, column tile) -- from an atomic queue; states are
+// ordered largest first.  Every output element is still written by exactly
+// one thread (the queue counter is the only atomic); each state's FP64
+// expectation partials land in its own slice and are reduced in a fixed order.
+// ---------------------------------------------------------------------------
+struct BatchDesc {
+    SectorView v;
+    Geom geo;
+    PlanDev p;
+    int64_t work0;      // first work unit of this state in the queue order
+    int64_t nwork;
+    int64_t part0;      // first 4-double partial slot of this state
+};
+
+struct BatchPtrs {
+    const void *in;
+    void *out;          // may be null (expectation only)
+};
+
+template <typename R, bool REALH, int TPT, int NBUF>
+__global__ void __launch_bounds__(kThreads)
+k_apply_batch(const BatchDesc *__restrict__ descs, const BatchPtrs *__restrict__ ptrs, int nstates,
+              int64_t total, unsigned long long *counter, double *__restrict__ partials, int want_out) {
+    using C2 = typename Cx<R>::T;
+    extern __shared__ __align__(16) char smem[];
+    __shared__ long long s_work;
+    for (;;) {
+        if (threadIdx.x == 0) s_work = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t work = s_work;
+        __syncthreads();
+        if (work >= total) break;
+        int lo = 0, hi = nstates - 1;  // last state with work0 <= work
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].work0 <= work) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchDesc &d = descs[lo];
+        const BatchPtrs bp = ptrs[lo];
+        const int64_t local = work - d.work0;
+        const int flags = ((want_out && bp.out) ? 1 : 0) | 2;
+        apply_unit<R, KBLK1, REALH, TPT, NBUF>(d.v, d.geo, d.p, local, static_cast<const C2 *>(bp.in),
+                                               static_cast<C2 *>(bp.out), partials + (d.part0 + local) * 4, flags,
+                                               smem);
+    }
+}
+
+// results[b][0..3] = fixed-order sum of state b's partials
+__global__ void __launch_bounds__(256) k_batch_reduce(const BatchDesc *__restrict__ descs, const double *partials,
+                                                      double *results) {
+    __shared__ double sm[4][256];
+    const BatchDesc &d = descs[blockIdx.x];
+    const int t = threadIdx.x;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = t; i < d.nwork; i += 256)
+        for (int k = 0; k < 4; ++k) s[k] += partials[(d.part0 + i) * 4 + k];
+    for (int k = 0; k < 4; ++k) sm[k][t] = s[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o)
+            for (int k = 0; k < 4; ++k) sm[k][t] += sm[k][t + o];
+        __syncthreads();
+    }
+    if (t < 4) results[(int64_t)blockIdx.x * 4 + t] = sm[t][0];
 }
 
 

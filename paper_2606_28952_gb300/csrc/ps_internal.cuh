@@ -100,6 +100,21 @@ struct SectorView {
 // apply plan: the canonical sum re-laid out for one sector split (rows = high
 // n - n_lo qubits, columns = low n_lo qubits)
 // ---------------------------------------------------------------------------
+// A launch shape chosen by the autotuner (0 / -1: decide automatically).
+struct LaunchChoice {
+    int tpt = 0;      // columns per thread: 1, 2 or 4
+    int nbuf = 0;     // staged source rows in flight: 1 or 2
+    int nsplit = 0;   // piece ranges per row: 1..16
+    int direct = -1;  // 1: direct gather (small plans), 0: staged
+};
+struct TunedEntry {
+    int64_t dim;
+    int nblk;
+    int dtype;
+    LaunchChoice choice;
+    double ms;
+};
+
 // Layout (all device arrays):
 //   piece p   : consecutive groups sharing x_hi (so one source row per CTA row),
 //               at most kItemsPerPiece items and kSegsPerPiece segments
@@ -123,6 +138,7 @@ struct Plan {
     double2 *t_c64 = nullptr;          // [M] FP64 coefficients
     float2 *t_c32 = nullptr;           // [M] FP32 coefficients
     std::vector<int64_t> h_pc_cumw;   // [P+1] cumulative per-piece work estimate
+    std::vector<TunedEntry> tuned;     // autotuned launch shapes per (sector, dtype)
     // reduction scratch for pauli_expect
     double *partials = nullptr;
     int64_t partials_cap = 0;
@@ -212,14 +228,17 @@ struct ApplyCfg {
     int64_t combine_nct = 0;
     bool direct = false;    // small plan: k_apply_direct (no staging, no split)
 };
-ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split);
+ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split,
+                      const LaunchChoice *force = nullptr);
 void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *psi_in,
-                  void *psi_out, int dtype, double *partials, cudaStream_t st, bool allow_split = true);
+                  void *psi_out, int dtype, double *partials, cudaStream_t st, bool allow_split = true,
+                  const LaunchChoice *force = nullptr);
 void launch_reduce(const double *partials, int64_t nparts, double *result, cudaStream_t st);
 // number of 4-double partial-sum slots an expectation launch writes
-int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow_split = true);
+int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow_split = true,
+                       const LaunchChoice *force = nullptr);
 // elements of the split scratch a launch needs (0: no split)
-int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype);
+int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype, const LaunchChoice *force = nullptr);
 void launch_rotate(pauli_sum *G, const SectorView &v, double theta, void *psi, int dtype,
                    cudaStream_t st);
 }  // namespace ps

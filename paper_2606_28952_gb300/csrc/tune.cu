@@ -1,0 +1,202 @@
+// tune.cu -- the autotuner of the apply launch shape: columns per thread,
+// staged source rows in flight, piece-range splits per row and direct vs
+// staged gather are timed on the device for one (operator, sector, dtype) and
+// the fastest is kept in the operator's plan for that sector.
+#include <algorithm>
+#include <cfloat>
+#include <cstdlib>
+#include <vector>
+
+#include "ps_internal.cuh"
+
+using namespace ps;
+
+namespace {
+
+int env_or(const char *name, int dflt) {
+    const char *e = std::getenv(name);
+    return (e && *e) ? std::atoi(e) : dflt;
+}
+
+void store_tuned(Plan &p, const SectorView &v, int dtype, const LaunchChoice &c, double ms) {
+    for (TunedEntry &t : p.tuned)
+        if (t.dim == v.dim && t.nblk == v.nblk && t.dtype == dtype) {
+            t.choice = c;
+            t.ms = ms;
+            return;
+        }
+    p.tuned.push_back(TunedEntry{v.dim, v.nblk, dtype, c, ms});
+}
+
+void ensure_split_capacity(pauli_sum *H, Plan &p, int64_t bytes) {
+    if (p.split_cap >= bytes) return;
+    PS_CUDA(cudaDeviceSynchronize());
+    dev_free(H->al, p.split_buf);
+    p.split_buf = nullptr;
+    p.split_cap = 0;
+    p.split_buf = dev_alloc(H->al, (size_t)bytes);
+    p.split_cap = bytes;
+}
+
+pauli_launch_config to_public(const ApplyCfg &c, double ms) {
+    pauli_launch_config o;
+    o.cols_per_thread = c.tpt;
+    o.staged_rows = c.nbuf;
+    o.row_split = c.nsplit;
+    o.direct = c.direct ? 1 : 0;
+    o.ms = ms;
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_launch_config *best,
+               pauli_stream_t st) {
+    try {
+        clear_error();
+        PS_CHECK(H && H->magic == kSumMagic, PAULI_EINVAL, "not a valid pauli_sum handle");
+        PS_CHECK(s && s->magic == kSectorMagic, PAULI_EINVAL, "not a valid pauli_sector handle");
+        PS_CHECK(H->n == s->v.n, PAULI_EINVAL, "operator and sector have different qubit counts");
+        PS_CHECK(dtype == PAULI_C64 || dtype == PAULI_C128, PAULI_EINVAL, "bad dtype");
+        PS_CHECK(reps >= 1 && reps <= 1000, PAULI_EINVAL, "reps must be in 1..1000");
+        cudaStream_t cs = (cudaStream_t)st;
+        Plan &p = get_plan(H, s->v.n_lo, cs);
+        const SectorView &v = s->v;
+        // candidates
+        std::vector<LaunchChoice> cand;
+        const bool fits = p.I <= 256 && p.S <= 1024;
+        for (int tpt : {1, 2, 4}) {
+            if (fits) {
+                LaunchChoice c;
+                c.tpt = tpt;
+                c.direct = 1;
+                cand.push_back(c);
+            }
+            for (int nbuf : {1, 2})
+                for (int ns : {1, 2, 4, 8, 16}) {
+                    if (ns > 1 && ns > std::max<int64_t>(1, p.P / 8)) continue;
+                    LaunchChoice c;
+                    c.tpt = tpt;
+                    c.nbuf = nbuf;
+                    c.nsplit = ns;
+                    c.direct = 0;
+                    const ApplyCfg cfg = apply_config(p, v, dtype, true, &c);
+                    if (cfg.nbuf != nbuf || cfg.nsplit != ns) continue;  // not realisable
+                    cand.push_back(c);
+                }
+        }
+        const int limit = env_or("PAULISIM_TUNE_MAX", 64);
+        if ((int)cand.size() > limit) cand.resize(limit);
+        // scratch states and the largest split buffer any candidate needs
+        const size_t es = dtype == PAULI_C64 ? 8 : 16;
+        int64_t need = 0;
+        for (const LaunchChoice &c : cand) need = std::max(need, apply_split_elems(p, v, dtype, &c) * (int64_t)es);
+        ensure_split_capacity(H, p, need);
+        DevBuf<char> in(H->al, (size_t)v.dim * es), out(H->al, (size_t)v.dim * es);
+        PS_CUDA(cudaMemsetAsync(in.p, 0x3c, (size_t)v.dim * es, cs));
+        cudaEvent_t e0, e1;
+        PS_CUDA(cudaEventCreate(&e0));
+        PS_CUDA(cudaEventCreate(&e1));
+        double best_ms = DBL_MAX;
+        LaunchChoice best_c;
+        ApplyCfg best_cfg;
+        try {
+            for (const LaunchChoice &c : cand) {
+                launch_apply(H, p, v, in.p, out.p, dtype, nullptr, cs, true, &c);  // warm-up
+                PS_CUDA(cudaEventRecord(e0, cs));
+                for (int r = 0; r < reps; ++r) launch_apply(H, p, v, in.p, out.p, dtype, nullptr, cs, true, &c);
+                PS_CUDA(cudaEventRecord(e1, cs));
+                PS_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                const double per = ms / reps;
+                if (per < best_ms) {
+                    best_ms = per;
+                    best_c = c;
+                    best_cfg = apply_config(p, v, dtype, true, &c);
+                }
+            }
+        } catch (...) {
+            (void)cudaEventDestroy(e0);
+            (void)cudaEventDestroy(e1);
+            throw;
+        }
+        (void)cudaEventDestroy(e0);
+        (void)cudaEventDestroy(e1);
+        PS_CUDA(cudaStreamSynchronize(cs));
+        store_tuned(p, v, dtype, best_c, best_ms);
+        if (best) *best = to_public(best_cfg, best_ms);
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PAULI_EINVAL;
+    }
+}
+
+int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, const pauli_launch_config *cfg) {
+    try {
+        clear_error();
+        PS_CHECK(H && H->magic == kSumMagic, PAULI_EINVAL, "not a valid pauli_sum handle");
+        PS_CHECK(s && s->magic == kSectorMagic, PAULI_EINVAL, "not a valid pauli_sector handle");
+        PS_CHECK(H->n == s->v.n, PAULI_EINVAL, "operator and sector have different qubit counts");
+        PS_CHECK(dtype == PAULI_C64 || dtype == PAULI_C128, PAULI_EINVAL, "bad dtype");
+        PS_CHECK(cfg != nullptr, PAULI_EINVAL, "cfg is NULL");
+        PS_CHECK(cfg->cols_per_thread == 1 || cfg->cols_per_thread == 2 || cfg->cols_per_thread == 4,
+                 PAULI_EINVAL, "cols_per_thread must be 1, 2 or 4");
+        PS_CHECK(cfg->staged_rows == 1 || cfg->staged_rows == 2, PAULI_EINVAL, "staged_rows must be 1 or 2");
+        PS_CHECK(cfg->row_split >= 1 && cfg->row_split <= 16, PAULI_EINVAL, "row_split must be in 1..16");
+        PS_CHECK(cfg->direct == 0 || cfg->direct == 1, PAULI_EINVAL, "direct must be 0 or 1");
+        cudaStream_t cs = nullptr;
+        PS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        try {
+            Plan &p = get_plan(H, s->v.n_lo, cs);
+            LaunchChoice c;
+            c.tpt = cfg->cols_per_thread;
+            c.nbuf = cfg->staged_rows;
+            c.nsplit = cfg->row_split;
+            c.direct = cfg->direct;
+            const size_t es = dtype == PAULI_C64 ? 8 : 16;
+            ensure_split_capacity(H, p, apply_split_elems(p, s->v, dtype, &c) * (int64_t)es);
+            store_tuned(p, s->v, dtype, c, cfg->ms);
+        } catch (...) {
+            (void)cudaStreamDestroy(cs);
+            throw;
+        }
+        PS_CUDA(cudaStreamSynchronize(cs));
+        (void)cudaStreamDestroy(cs);
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PAULI_EINVAL;
+    }
+}
+
+int pauli_get_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, pauli_launch_config *cfg) {
+    try {
+        clear_error();
+        PS_CHECK(H && H->magic == kSumMagic, PAULI_EINVAL, "not a valid pauli_sum handle");
+        PS_CHECK(s && s->magic == kSectorMagic, PAULI_EINVAL, "not a valid pauli_sector handle");
+        PS_CHECK(dtype == PAULI_C64 || dtype == PAULI_C128, PAULI_EINVAL, "bad dtype");
+        PS_CHECK(cfg != nullptr, PAULI_EINVAL, "cfg is NULL");
+        Plan *p = find_plan(H, s->v.n_lo);
+        PS_CHECK(p != nullptr, PAULI_EINVAL, "no plan for this sector split yet: call pauli_prepare first");
+        double ms = 0.0;
+        for (const TunedEntry &t : p->tuned)
+            if (t.dim == s->v.dim && t.nblk == s->v.nblk && t.dtype == dtype) ms = t.ms;
+        *cfg = to_public(apply_config(*p, s->v, dtype, true), ms);
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    }
+}
+
+}  // extern "C"
