@@ -236,14 +236,17 @@ int pauli_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, i
 
 /* Launch shape of pauli_apply / pauli_expect for one (operator, sector, dtype):
  * columns (targets) per thread, staged source rows in flight, piece ranges a
- * row is split into (their partial vectors are added in a fixed order), and
+ * row is split into (their partial vectors are added in a fixed order),
  * direct gather (operators small enough to keep whole in shared memory) vs
- * staged source rows.  ms: measured time of one apply (0 if not measured). */
+ * staged source rows, and (single-block sectors) rows staged densely by rank
+ * with a rank table vs by bit pattern.  ms: measured time of one apply (0 if
+ * not measured). */
 typedef struct {
     int cols_per_thread;  /* 1, 2 or 4 */
     int staged_rows;      /* 1 or 2 */
     int row_split;        /* 1..16 */
     int direct;           /* 0 or 1 */
+    int ranked;           /* 0 or 1 */
     double ms;
 } pauli_launch_config;
 

@@ -345,7 +345,7 @@ def expect_noalloc(H: PauliSum, s: Sector, psi, result, hpsi_out=None, stream=No
 
 class LaunchConfig(C.Structure):
     _fields_ = [("cols_per_thread", C.c_int), ("staged_rows", C.c_int), ("row_split", C.c_int),
-                ("direct", C.c_int), ("ms", C.c_double)]
+                ("direct", C.c_int), ("ranked", C.c_int), ("ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

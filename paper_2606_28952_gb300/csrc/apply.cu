@@ -144,20 +144,30 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     LaunchChoice ch;
     if (force) ch = *force;
     else if (const LaunchChoice *t = find_tuned(p, v, dtype)) ch = *t;
-    const int rw = 1 << v.n_lo;
-    const size_t bb = dtype == PAULI_C64 ? Smem<float>::buf_bytes(rw) : Smem<double>::buf_bytes(rw);
+    auto buf_bytes = [&](int cap) {
+        return dtype == PAULI_C64 ? Smem<float>::buf_bytes(cap) : Smem<double>::buf_bytes(cap);
+    };
     int64_t mx = 0;
     for (int b = 0; b < v.nblk; ++b) mx = std::max(mx, v.dlo[b]);
+    // rows staged by bit pattern need 2^n_lo slots; a single block can instead
+    // be staged densely by rank (D_lo slots) plus a rank table
+    const bool single = v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1;
+    const size_t bb_pattern = buf_bytes(1 << v.n_lo);
+    const bool rank_ok = single && v.n_lo <= 16;
+    const int dflt_ranked = env_int("PAULISIM_RANKED", (single && bb_pattern > kMaxDynSmem) ? 1 : 0);
+    c.ranked = rank_ok && (ch.ranked >= 0 ? ch.ranked != 0 : dflt_ranked != 0);
+    const size_t bb = c.ranked ? buf_bytes(ranked_rowcap(v.dlo[0])) : bb_pattern;
+    const size_t extra = c.ranked ? rank_table_bytes(v.n_lo) : 0;
     // measured on the 24-qubit molecule (D_lo = 924): 4 columns per thread and a
     // single staged row (more resident CTAs) beat finer tiles and double buffering
     int tpt = ch.tpt ? ch.tpt : env_int("PAULISIM_TPT", mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1));
     if (tpt != 1 && tpt != 2 && tpt != 4) tpt = 1;
     int nbuf = ch.nbuf ? ch.nbuf : env_int("PAULISIM_NBUF", 1);
     if (nbuf != 1 && nbuf != 2) nbuf = 1;
-    if (nbuf * bb > kMaxDynSmem) nbuf = 1;
+    if (nbuf * bb + extra > kMaxDynSmem) nbuf = 1;
     c.tpt = tpt;
     c.nbuf = nbuf;
-    c.smem = nbuf * bb;
+    c.smem = nbuf * bb + extra;
     c.base_nct = make_geom(v, tpt * kThreads).cta_off[v.nblk];
     // small operators (lattice models): the whole folded plan fits in shared
     // memory and rows have few pieces, so gather straight from global memory

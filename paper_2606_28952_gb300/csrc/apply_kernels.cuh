@@ -134,7 +134,19 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-enum : int { KFULL = 0, KBLK1 = 1, KBLKN = 2 };
+// KFULL: full space; KBLK1 / KBLKN: one / several product blocks, source rows
+// staged by bit pattern (2^n_lo slots, zeros outside the block); KBLKR: one
+// product block, source rows staged densely by rank and found through a rank
+// table in shared memory (for splits too wide for 2^n_lo slots).
+enum : int { KFULL = 0, KBLK1 = 1, KBLKN = 2, KBLKR = 3 };
+
+// Rank table of KBLKR: n_lo <= 14: u16 lut[2^n_lo] (D_lo, the zero slot, for
+// strings outside the block); 15..16: u32 tabA[256] (colex rank of the low
+// byte) and tabB[256][9] (what the high byte adds, by the low byte's popcount).
+__host__ __device__ inline size_t rank_table_bytes(int n_lo) {
+    return n_lo <= 14 ? ((size_t)2 << n_lo) : (size_t)(256 + 256 * 9) * 4;
+}
+__host__ __device__ inline int ranked_rowcap(int64_t dlo) { return (int)((dlo + 2) & ~1ll); }
 
 constexpr int kSegCap = PlanLimits::kSegsPerPiece;
 constexpr int kItemCap = PlanLimits::kItemsPerPiece;
@@ -194,6 +206,12 @@ __device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &
             for (int64_t r = tid; r < len; r += nth) cp_async16(B.row + r, psi + base + r);
         } else {
             for (int64_t r = 2 * tid; r < len; r += 2 * nth) cp_async16(B.row + r, psi + base + r);
+        }
+    } else if (KIND == KBLKR) {
+        // dense copy of the source row, indexed later through the rank table
+        for (int64_t r = tid; r < len; r += nth) {
+            if (sizeof(C2) == 16) cp_async16(B.row + r, psi + base + r);
+            else cp_async8(B.row + r, psi + base + r);
         }
     } else {
         const uint32_t *lst = v.list_lo + v.list_lo_off[klo];
@@ -257,9 +275,25 @@ __device__ __forceinline__ int next_piece(const SectorView &v, const PlanDev &p,
     return q;
 }
 
+// Rank lookup of KBLKR (see rank_table_bytes).
+struct RankTab {
+    const uint16_t *lut;
+    const uint32_t *tabA, *tabB;
+    int n_lo, klo;
+    uint32_t dlo;
+};
+
+__device__ __forceinline__ uint32_t ranked_index(const RankTab &rt, uint32_t s) {
+    if (rt.n_lo <= 14) return rt.lut[s];
+    const uint32_t lo8 = s & 255u;
+    const uint32_t r = rt.tabA[lo8] + rt.tabB[(s >> 8) * 9 + __popc(lo8)];
+    return __popc(s) == rt.klo ? r : rt.dlo;
+}
+
 template <typename R, int KIND, bool REALH, int TPT>
 __device__ __forceinline__ void gather_piece(const PlanDev &p, int q, const Buf<R> &B, int klo_req,
-                                             const uint32_t (&tlo)[TPT], R (&accr)[TPT], R (&acci)[TPT]) {
+                                             const uint32_t (&tlo)[TPT], R (&accr)[TPT], R (&acci)[TPT],
+                                             const RankTab &rt) {
     using C2 = typename Cx<R>::T;
     const int nit = __ldg(p.pc_i0 + q + 1) - __ldg(p.pc_i0 + q);
     for (int it = 0; it < nit; ++it) {
@@ -318,7 +352,7 @@ __device__ __forceinline__ void gather_piece(const PlanDev &p, int q, const Buf<
         }
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
-            C2 amp = B.row[s[j]];
+            C2 amp = B.row[(KIND == KBLKR) ? ranked_index(rt, s[j]) : s[j]];
             if (KIND == KBLKN && __popc(s[j]) != klo_req) {
                 amp.x = R(0);
                 amp.y = R(0);
@@ -344,13 +378,47 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
                                            int flags, char *smem) {
     using C2 = typename Cx<R>::T;
     __shared__ int klo_req[2];
-    const int rw = 1 << v.n_lo;
+    const int rw = (KIND == KBLKR) ? ranked_rowcap(v.dlo[0]) : (1 << v.n_lo);
     const size_t bb = Smem<R>::buf_bytes(rw);
     Buf<R> B0(smem, rw), B1(smem + (NBUF > 1 ? bb : 0), rw);
     const RowCtx rc = decode_row<KIND == KFULL>(v, geo, work);
     const int tid = threadIdx.x;
 
-    if (KIND != KFULL) {
+    RankTab rt;
+    rt.lut = nullptr;
+    rt.tabA = rt.tabB = nullptr;
+    rt.n_lo = v.n_lo;
+    rt.klo = v.klo[0];
+    rt.dlo = (uint32_t)v.dlo[0];
+    if (KIND == KBLKR) {
+        char *tab = smem + (size_t)NBUF * bb;
+        rt.lut = reinterpret_cast<const uint16_t *>(tab);
+        rt.tabA = reinterpret_cast<const uint32_t *>(tab);
+        rt.tabB = rt.tabA + 256;
+        const int klo = v.klo[0];
+        const int64_t dlo = v.dlo[0];
+        if (v.n_lo <= 14) {
+            uint16_t *lut = reinterpret_cast<uint16_t *>(tab);
+            for (int s = tid; s < (1 << v.n_lo); s += kThreads)
+                lut[s] = (uint16_t)(__popc(s) == klo ? __ldg(v.rank_lo + s) : (uint32_t)dlo);
+        } else {
+            uint32_t *tabA = reinterpret_cast<uint32_t *>(tab);
+            uint32_t *tabB = tabA + 256;
+            for (int s = tid; s < 256; s += kThreads) tabA[s] = __ldg(v.rank_lo + s);
+            for (int e = tid; e < 256 * 9; e += kThreads) {
+                const uint32_t h = (uint32_t)(e / 9), k0 = (uint32_t)(e % 9);
+                const uint32_t s = (h << 8) | ((1u << k0) - 1u);
+                tabB[e] = (h < (1u << (v.n_lo - 8))) ? __ldg(v.rank_lo + s) : 0u;
+            }
+        }
+        C2 zz;
+        zz.x = R(0);
+        zz.y = R(0);
+        if (tid == 0) {
+            B0.row[dlo] = zz;  // the zero slot
+            if (NBUF > 1) B1.row[dlo] = zz;
+        }
+    } else if (KIND != KFULL) {
         // slots outside the source block stay zero
         for (int r = tid; r < rw; r += kThreads) {
             C2 zz;
@@ -388,7 +456,7 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
                 cp_async_wait<0>();
             }
             __syncthreads();
-            gather_piece<R, KIND, REALH, TPT>(p, q, c ? B1 : B0, klo_req[c], tlo, accr, acci);
+            gather_piece<R, KIND, REALH, TPT>(p, q, c ? B1 : B0, klo_req[c], tlo, accr, acci, rt);
             __syncthreads();
             c ^= 1;
             q = qn;
@@ -398,7 +466,7 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
             stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
             cp_async_wait<0>();
             __syncthreads();
-            gather_piece<R, KIND, REALH, TPT>(p, q, B0, klo_req[0], tlo, accr, acci);
+            gather_piece<R, KIND, REALH, TPT>(p, q, B0, klo_req[0], tlo, accr, acci, rt);
             __syncthreads();
             q = next_piece<R, KIND>(v, p, q, rc.thi, pend);
         }
@@ -482,7 +550,7 @@ struct BatchPtrs {
     void *out;          // may be null (expectation only)
 };
 
-template <typename R, bool REALH, int TPT, int NBUF>
+template <typename R, int KIND, bool REALH, int TPT, int NBUF>
 __global__ void __launch_bounds__(kThreads)
 k_apply_batch(const BatchDesc *__restrict__ descs, const BatchPtrs *__restrict__ ptrs, int nstates,
               int64_t total, unsigned long long *counter, double *__restrict__ partials, int want_out) {
@@ -505,7 +573,7 @@ k_apply_batch(const BatchDesc *__restrict__ descs, const BatchPtrs *__restrict__
         const BatchPtrs bp = ptrs[lo];
         const int64_t local = work - d.work0;
         const int flags = ((want_out && bp.out) ? 1 : 0) | 2;
-        apply_unit<R, KBLK1, REALH, TPT, NBUF>(d.v, d.geo, d.p, local, static_cast<const C2 *>(bp.in),
+        apply_unit<R, KIND, REALH, TPT, NBUF>(d.v, d.geo, d.p, local, static_cast<const C2 *>(bp.in),
                                                static_cast<C2 *>(bp.out), partials + (d.part0 + local) * 4, flags,
                                                smem);
     }
@@ -908,7 +976,7 @@ void launch_apply_prec(const ApplyCfg &cfg, const Plan &p, const SectorView &v, 
     using C2 = typename Cx<R>::T;
     const Geom geo = make_geom(v, cfg.tpt * kThreads, cfg.nsplit, cfg.split_p0.data(), (int32_t)p.P);
     const PlanDev pd = plan_dev(p);
-    const int kind = v.kind == PAULI_SECTOR_FULL ? KFULL : (v.nblk == 1 ? KBLK1 : KBLKN);
+    const int kind = v.kind == PAULI_SECTOR_FULL ? KFULL : (v.nblk == 1 ? (cfg.ranked ? KBLKR : KBLK1) : KBLKN);
     void *kout = out;
     int flags = (out ? 1 : 0) | (partials ? 2 : 0);
     if (cfg.nsplit > 1) {
@@ -918,10 +986,12 @@ void launch_apply_prec(const ApplyCfg &cfg, const Plan &p, const SectorView &v, 
     if (p.real) {
         if (kind == KFULL) launch_kind<R, KFULL, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
         else if (kind == KBLK1) launch_kind<R, KBLK1, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else if (kind == KBLKR) launch_kind<R, KBLKR, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
         else launch_kind<R, KBLKN, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
     } else {
         if (kind == KFULL) launch_kind<R, KFULL, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
         else if (kind == KBLK1) launch_kind<R, KBLK1, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else if (kind == KBLKR) launch_kind<R, KBLKR, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
         else launch_kind<R, KBLKN, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
     }
     if (cfg.nsplit > 1) {

@@ -19,8 +19,10 @@ struct pauli_batch {
     std::vector<int> order;           // queue position -> state
     std::vector<int64_t> rw_bits;     // n_lo per state
     int max_nlo = 0;
+    int64_t max_dlo = 0;
     int64_t total = 0;                // work units of one launch
     int tpt = 0, nbuf = 1;            // launch shape (0: not chosen yet)
+    bool ranked = false;              // rows staged by rank (wide splits)
     BatchDesc *d_desc = nullptr;      // [n] in queue order
     BatchPtrs *d_ptrs = nullptr;      // [n]
     double *d_partials = nullptr;     // [total][4]
@@ -38,9 +40,9 @@ int env_int2(const char *name, int dflt) {
     return (e && *e) ? std::atoi(e) : dflt;
 }
 
-template <typename R, bool REALH, int TPT, int NBUF>
+template <typename R, int KIND, bool REALH, int TPT, int NBUF>
 void launch_batch_t(pauli_batch *b, size_t smem, double *results, bool want_out, cudaStream_t st) {
-    auto kern = k_apply_batch<R, REALH, TPT, NBUF>;
+    auto kern = k_apply_batch<R, KIND, REALH, TPT, NBUF>;
     PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
     PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
@@ -56,11 +58,20 @@ void launch_batch_t(pauli_batch *b, size_t smem, double *results, bool want_out,
     PS_LAUNCH_CHECK();
 }
 
-template <typename R, bool REALH>
-void launch_batch_r(pauli_batch *b, int tpt, int nbuf, double *results, bool want_out, cudaStream_t st) {
-    const size_t smem = (size_t)nbuf * Smem<R>::buf_bytes(1 << b->max_nlo);
+// Dynamic shared memory of the batched launch: the widest state decides.
+size_t batch_smem(const pauli_batch *b, int nbuf, bool ranked) {
+    auto bb = [&](int cap) {
+        return b->dtype == PAULI_C64 ? Smem<float>::buf_bytes(cap) : Smem<double>::buf_bytes(cap);
+    };
+    if (!ranked) return (size_t)nbuf * bb(1 << b->max_nlo);
+    return (size_t)nbuf * bb(ranked_rowcap(b->max_dlo)) + rank_table_bytes(b->max_nlo);
+}
+
+template <typename R, int KIND, bool REALH>
+void launch_batch_k(pauli_batch *b, int tpt, int nbuf, double *results, bool want_out, cudaStream_t st) {
+    const size_t smem = batch_smem(b, nbuf, KIND == KBLKR);
     PS_CHECK(smem <= 226 * 1024, PAULI_EUNSUPPORTED, "batched apply: the widest sector split is too wide");
-#define PS_B(T, N) launch_batch_t<R, REALH, T, N>(b, smem, results, want_out, st)
+#define PS_B(T, N) launch_batch_t<R, KIND, REALH, T, N>(b, smem, results, want_out, st)
     if (nbuf == 2) {
         if (tpt == 4) PS_B(4, 2); else if (tpt == 2) PS_B(2, 2); else PS_B(1, 2);
     } else {
@@ -69,14 +80,20 @@ void launch_batch_r(pauli_batch *b, int tpt, int nbuf, double *results, bool wan
 #undef PS_B
 }
 
-void launch_batch(pauli_batch *b, int tpt, int nbuf, double *results, bool want_out, cudaStream_t st) {
-    if (b->dtype == PAULI_C64) {
-        if (b->realh) launch_batch_r<float, true>(b, tpt, nbuf, results, want_out, st);
-        else launch_batch_r<float, false>(b, tpt, nbuf, results, want_out, st);
+template <typename R>
+void launch_batch_r(pauli_batch *b, int tpt, int nbuf, bool ranked, double *results, bool want_out, cudaStream_t st) {
+    if (ranked) {
+        if (b->realh) launch_batch_k<R, KBLKR, true>(b, tpt, nbuf, results, want_out, st);
+        else launch_batch_k<R, KBLKR, false>(b, tpt, nbuf, results, want_out, st);
     } else {
-        if (b->realh) launch_batch_r<double, true>(b, tpt, nbuf, results, want_out, st);
-        else launch_batch_r<double, false>(b, tpt, nbuf, results, want_out, st);
+        if (b->realh) launch_batch_k<R, KBLK1, true>(b, tpt, nbuf, results, want_out, st);
+        else launch_batch_k<R, KBLK1, false>(b, tpt, nbuf, results, want_out, st);
     }
+}
+
+void launch_batch(pauli_batch *b, int tpt, int nbuf, bool ranked, double *results, bool want_out, cudaStream_t st) {
+    if (b->dtype == PAULI_C64) launch_batch_r<float>(b, tpt, nbuf, ranked, results, want_out, st);
+    else launch_batch_r<double>(b, tpt, nbuf, ranked, results, want_out, st);
 }
 
 // (Re)build the descriptors for a columns-per-thread value.
@@ -162,7 +179,9 @@ int pauli_batch_create(int n, pauli_sum *const *H, const pauli_sector *const *S,
                 b->S.push_back(S[i]);
                 b->realh = b->realh && H[i]->real;
                 b->max_nlo = std::max(b->max_nlo, S[i]->v.n_lo);
+                b->max_dlo = std::max<int64_t>(b->max_dlo, S[i]->v.dlo[0]);
             }
+            PS_CHECK(b->max_nlo <= 16, PAULI_EUNSUPPORTED, "batch: the low half of a split is wider than 16 qubits");
             b->d_desc = static_cast<BatchDesc *>(dev_alloc(b->al, sizeof(BatchDesc) * n));
             b->d_ptrs = static_cast<BatchPtrs *>(dev_alloc(b->al, sizeof(BatchPtrs) * n));
             b->d_results = static_cast<double *>(dev_alloc(b->al, sizeof(double) * 4 * n));
@@ -174,6 +193,7 @@ int pauli_batch_create(int n, pauli_sum *const *H, const pauli_sector *const *S,
             const int tpt = env_int2("PAULISIM_TPT", mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1));
             build_descs(b, (tpt == 1 || tpt == 2 || tpt == 4) ? tpt : 1);
             b->nbuf = 1;
+            b->ranked = batch_smem(b, 1, false) > 226 * 1024;
         } catch (...) {
             dev_free(b->al, b->d_desc);
             dev_free(b->al, b->d_ptrs);
@@ -213,7 +233,7 @@ int pauli_batch_apply(pauli_batch *b, const void *const *psi_in, void *const *ps
         }
         cudaStream_t cs = (cudaStream_t)st;
         upload_ptrs(b, psi_in, psi_out, cs);
-        launch_batch(b, b->tpt, b->nbuf, b->d_results, psi_out != nullptr, cs);
+        launch_batch(b, b->tpt, b->nbuf, b->ranked, b->d_results, psi_out != nullptr, cs);
         if (results) {  // results in the caller's state order
             k_unpermute<<<(b->n + 127) / 128, 128, 0, cs>>>(b->d_results, b->d_order, b->n, results);
             PS_LAUNCH_CHECK();
@@ -241,29 +261,29 @@ int pauli_batch_tune(pauli_batch *b, const void *const *psi_in, void *const *psi
         PS_CUDA(cudaEventCreate(&e1));
         double best_ms = DBL_MAX;
         int bt = b->tpt, bn = b->nbuf;
+        bool br = b->ranked;
         try {
             for (int tpt : {1, 2, 4}) {
                 build_descs(b, tpt);
                 upload_ptrs(b, psi_in, psi_out, cs);
-                for (int nbuf : {1, 2}) {
-                    const size_t es = b->dtype == PAULI_C64 ? 8 : 16;
-                    const size_t smem = (size_t)nbuf * (b->dtype == PAULI_C64 ? Smem<float>::buf_bytes(1 << b->max_nlo)
-                                                                               : Smem<double>::buf_bytes(1 << b->max_nlo));
-                    (void)es;
-                    if (smem > 226 * 1024) continue;
-                    launch_batch(b, tpt, nbuf, b->d_results, psi_out != nullptr, cs);
-                    PS_CUDA(cudaEventRecord(e0, cs));
-                    for (int r = 0; r < reps; ++r) launch_batch(b, tpt, nbuf, b->d_results, psi_out != nullptr, cs);
-                    PS_CUDA(cudaEventRecord(e1, cs));
-                    PS_CUDA(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    if (ms / reps < best_ms) {
-                        best_ms = ms / reps;
-                        bt = tpt;
-                        bn = nbuf;
+                for (int ranked : {0, 1})
+                    for (int nbuf : {1, 2}) {
+                        if (batch_smem(b, nbuf, ranked != 0) > 226 * 1024) continue;
+                        launch_batch(b, tpt, nbuf, ranked != 0, b->d_results, psi_out != nullptr, cs);
+                        PS_CUDA(cudaEventRecord(e0, cs));
+                        for (int r = 0; r < reps; ++r)
+                            launch_batch(b, tpt, nbuf, ranked != 0, b->d_results, psi_out != nullptr, cs);
+                        PS_CUDA(cudaEventRecord(e1, cs));
+                        PS_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                        if (ms / reps < best_ms) {
+                            best_ms = ms / reps;
+                            bt = tpt;
+                            bn = nbuf;
+                            br = ranked != 0;
+                        }
                     }
-                }
             }
         } catch (...) {
             (void)cudaEventDestroy(e0);
@@ -274,11 +294,13 @@ int pauli_batch_tune(pauli_batch *b, const void *const *psi_in, void *const *psi
         (void)cudaEventDestroy(e1);
         build_descs(b, bt);
         b->nbuf = bn;
+        b->ranked = br;
         if (best) {
             best->cols_per_thread = bt;
             best->staged_rows = bn;
             best->row_split = 1;
             best->direct = 0;
+            best->ranked = br ? 1 : 0;
             best->ms = best_ms;
         }
         return PAULI_OK;

@@ -106,6 +106,7 @@ struct LaunchChoice {
     int nbuf = 0;     // staged source rows in flight: 1 or 2
     int nsplit = 0;   // piece ranges per row: 1..16
     int direct = -1;  // 1: direct gather (small plans), 0: staged
+    int ranked = -1;  // 1: rows staged by rank + rank table, 0: by bit pattern
 };
 struct TunedEntry {
     int64_t dim;
@@ -227,6 +228,7 @@ struct ApplyCfg {
     int64_t nct = 0;        // CTAs of the gather launch = base_nct * nsplit
     int64_t combine_nct = 0;
     bool direct = false;    // small plan: k_apply_direct (no staging, no split)
+    bool ranked = false;    // single block, rows staged by rank (KBLKR)
 };
 ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split,
                       const LaunchChoice *force = nullptr);

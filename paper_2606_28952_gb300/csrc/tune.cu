@@ -44,6 +44,7 @@ pauli_launch_config to_public(const ApplyCfg &c, double ms) {
     o.staged_rows = c.nbuf;
     o.row_split = c.nsplit;
     o.direct = c.direct ? 1 : 0;
+    o.ranked = c.ranked ? 1 : 0;
     o.ms = ms;
     return o;
 }
@@ -74,18 +75,22 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
                 c.direct = 1;
                 cand.push_back(c);
             }
-            for (int nbuf : {1, 2})
-                for (int ns : {1, 2, 4, 8, 16}) {
-                    if (ns > 1 && ns > std::max<int64_t>(1, p.P / 8)) continue;
-                    LaunchChoice c;
-                    c.tpt = tpt;
-                    c.nbuf = nbuf;
-                    c.nsplit = ns;
-                    c.direct = 0;
-                    const ApplyCfg cfg = apply_config(p, v, dtype, true, &c);
-                    if (cfg.nbuf != nbuf || cfg.nsplit != ns) continue;  // not realisable
-                    cand.push_back(c);
-                }
+            for (int ranked : {0, 1})
+                for (int nbuf : {1, 2})
+                    for (int ns : {1, 2, 4, 8, 16}) {
+                        if (ns > 1 && ns > std::max<int64_t>(1, p.P / 8)) continue;
+                        LaunchChoice c;
+                        c.tpt = tpt;
+                        c.nbuf = nbuf;
+                        c.nsplit = ns;
+                        c.direct = 0;
+                        c.ranked = ranked;
+                        const ApplyCfg cfg = apply_config(p, v, dtype, true, &c);
+                        // not realisable, or the layout does not fit in shared memory
+                        if (cfg.nbuf != nbuf || cfg.nsplit != ns || (int)cfg.ranked != ranked) continue;
+                        if (cfg.smem > 226 * 1024) continue;
+                        cand.push_back(c);
+                    }
         }
         const int limit = env_or("PAULISIM_TUNE_MAX", 64);
         if ((int)cand.size() > limit) cand.resize(limit);
@@ -151,6 +156,7 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
         PS_CHECK(cfg->staged_rows == 1 || cfg->staged_rows == 2, PAULI_EINVAL, "staged_rows must be 1 or 2");
         PS_CHECK(cfg->row_split >= 1 && cfg->row_split <= 16, PAULI_EINVAL, "row_split must be in 1..16");
         PS_CHECK(cfg->direct == 0 || cfg->direct == 1, PAULI_EINVAL, "direct must be 0 or 1");
+        PS_CHECK(cfg->ranked == 0 || cfg->ranked == 1, PAULI_EINVAL, "ranked must be 0 or 1");
         cudaStream_t cs = nullptr;
         PS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         try {
@@ -160,6 +166,7 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
             c.nbuf = cfg->staged_rows;
             c.nsplit = cfg->row_split;
             c.direct = cfg->direct;
+            c.ranked = cfg->ranked;
             const size_t es = dtype == PAULI_C64 ? 8 : 16;
             ensure_split_capacity(H, p, apply_split_elems(p, s->v, dtype, &c) * (int64_t)es);
             store_tuned(p, s->v, dtype, c, cfg->ms);

@@ -94,6 +94,46 @@ def test_apply_multiblock_sz0_xxz(ps, dt):
     assert _rel(out, ref) <= TOL[dt]
 
 
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("norb,na,nb", [(16, 1, 1), (16, 2, 1), (15, 2, 2), (14, 2, 1)])
+def test_apply_wide_split_rank_staged(ps, dt, norb, na, nb):
+    """Low half of 14-16 qubits: rows staged densely by rank (full u16 rank table
+    up to 14 bits, byte-split tables above)."""
+    h, g = w.molecular_integrals(norb, 2)
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    R = oracle.jw_hamiltonian(norb, h, g, eps_drop=1e-12)
+    S = ps.Sector.molecular(norb, na, nb)
+    So = oracle.Sector.molecular(norb, na, nb)
+    psi = w.random_state(S.dim, 5)
+    x = _to_dev(psi, dt)
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    ref = oracle.apply(So, R, x.cpu().numpy().astype(np.complex128))
+    assert _rel(out, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_apply_rank_staged_matches_pattern_staged(ps, dt):
+    """The two staging layouts (forced through the launch-shape interface) agree with the oracle."""
+    import torch
+    h, g, R = _mol(8, 4, 4)
+    S = ps.Sector.molecular(8, 4, 4)
+    So = oracle.Sector.molecular(8, 4, 4)
+    psi = w.random_state(S.dim, 12)
+    code = ps.C64 if dt == "c64" else ps.C128
+    for ranked in (0, 1):
+        H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+        ps.prepare(H, S)
+        c = ps.LaunchConfig(cols_per_thread=1, staged_rows=1, row_split=2, direct=0, ranked=ranked, ms=0.0)
+        ps._check(ps.lib().pauli_set_launch_config(H._h, S._h, code, ps.C.byref(c)))
+        assert ps.launch_config(H, S, torch.complex64 if dt == "c64" else torch.complex128)["ranked"] == ranked
+        x = _to_dev(psi, dt)
+        out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+        assert _rel(out, oracle.apply(So, R, x.cpu().numpy().astype(np.complex128))) <= TOL[dt]
+        r = ps.expect(H, S, x).cpu().numpy()
+        E, _ = oracle.expect(So, R, x.cpu().numpy().astype(np.complex128))
+        assert abs(complex(r[0], r[1]) - E) <= (1e-12 if dt == "c128" else 1e-6)
+
+
 def test_apply_edge_cases(ps):
     import torch
     # empty operator -> zero vector

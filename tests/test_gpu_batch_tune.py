@@ -97,7 +97,7 @@ def test_tune_single_and_cache(ps, tmp_path):
     # an explicitly installed shape is used and still exact
     H3 = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
     ps.prepare(H3, S)
-    c = ps.LaunchConfig(1, 2, 3, 0, 0.0)
+    c = ps.LaunchConfig(cols_per_thread=1, staged_rows=2, row_split=3, direct=0, ranked=0, ms=0.0)
     ps._check(ps.lib().pauli_set_launch_config(H3._h, S._h, ps.C128, ps.C.byref(c)))
     got = ps.launch_config(H3, S, torch.complex128)
     assert (got["cols_per_thread"], got["staged_rows"], got["row_split"]) == (1, 2, 3)
