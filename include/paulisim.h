@@ -230,6 +230,75 @@ int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const void *psi, i
 int pauli_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, int dtype,
                  pauli_stream_t st);
 
+/* One step of the adjoint (reverse-mode) gradient of a product ansatz
+ * psi(theta) = U_K ... U_1 psi_0, U_k = exp(-i theta_k G_k) (Sec. 3.2):
+ * result[0] + i result[1] = <lam|G|phi> from the input vectors (FP64,
+ * fixed reduction order; result is a DEVICE array of 2 doubles), then
+ * phi <- exp(-i theta G) phi and lam <- exp(-i theta G) lam in place, in one
+ * pass over both vectors.  With phi = psi(theta), lam = H psi(theta) and
+ * k = K..1 called with theta = -theta_k, dE/dtheta_k = 2 Im result_k.
+ * Same generator rules and sector-leak status as pauli_rotate; phi != lam.
+ * Uses the per-device scratch of pauli_vdot (see there). */
+int pauli_rotate_adjoint(pauli_sum *G, const pauli_sector *s, double theta, void *phi, void *lam, int dtype,
+                         double *result, pauli_stream_t st);
+
+/* psi <- exp(-i theta_{k-1} G_{k-1}) ... exp(-i theta_0 G_0) psi: k calls of
+ * pauli_rotate in order (a product-form ansatz, Sec. 3.2); stops at the first
+ * error and returns it.  Gs: host array of k handles, thetas: host array. */
+int pauli_rotate_seq(pauli_sum *const *Gs, const double *thetas, int k, const pauli_sector *s, void *psi,
+                     int dtype, pauli_stream_t st);
+
+/* result[0] + i result[1] = <x|y> = sum_i conj(x_i) y_i over n amplitudes of
+ * type dtype, accumulated in FP64 in a fixed order (the same inputs give the
+ * same bits); result is a DEVICE array of 2 doubles written on st.  x, y
+ * 16-byte aligned device vectors (may be NULL if n == 0).  The per-block partial sums go to one
+ * scratch array per device (8 x 4 doubles per SM), allocated on the first
+ * call and kept until exit and shared with pauli_rotate_adjoint: calls of the
+ * two issued on different streams must be ordered with events. */
+int pauli_vdot(const void *x, const void *y, int64_t n, int dtype, double *result, pauli_stream_t st);
+
+/* ------------------------------------------------------------------------- */
+/* learned warm start: a small multilayer perceptron on the tensor cores      */
+/* ------------------------------------------------------------------------- */
+
+/* y = W3^T tanh(W2^T tanh(W1^T x + b1) + b2) + b3 mapping a geometry
+ * descriptor (in_dim values, e.g. a bond length) to the out_dim ansatz
+ * amplitudes that start the variational optimisation at that geometry
+ * (the learned warm start of Sec. 4).  The two hidden-width products run in
+ * BF16 on the tensor cores with FP32 accumulation; master weights, biases,
+ * the first layer and Adam are FP32.  Parameter vector layout (FP32):
+ * W1[in][hid], b1[hid], W2[hid][hid], b2[hid], W3[hid][out], b3[out],
+ * row-major, W[k][j] multiplying input k into output j.  A new network has
+ * all parameters zero; set them with pauli_mlp_set_params. */
+typedef struct pauli_mlp pauli_mlp;
+int pauli_mlp_create(int in_dim, int hidden, int out_dim, int max_batch, pauli_mlp **out);
+int pauli_mlp_num_params(const pauli_mlp *m, int64_t *n);
+/* host <-> device copies of the parameter vector (set also zeroes Adam's moments); blocking */
+int pauli_mlp_set_params(pauli_mlp *m, const float *params);
+int pauli_mlp_get_params(const pauli_mlp *m, float *params);
+
+/* y[batch][out] = net(x[batch][in]); x, y DEVICE FP32 arrays; 1 <= batch <= max_batch */
+int pauli_mlp_forward(pauli_mlp *m, int batch, const float *x, float *y, pauli_stream_t st);
+
+/* Forward pass, loss = 1/(2 batch) sum (y - target)^2 (device double, if loss
+ * is not NULL) and its gradient with respect to every parameter, kept in the
+ * handle for pauli_mlp_adam_step and copied to the DEVICE array grads (same
+ * layout as the parameters) if grads is not NULL. */
+int pauli_mlp_backward(pauli_mlp *m, int batch, const float *x, const float *target, float *grads,
+                       double *loss, pauli_stream_t st);
+
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected for step
+ * t >= 1) with the gradient of the last pauli_mlp_backward. */
+int pauli_mlp_adam_step(pauli_mlp *m, float lr, int t, pauli_stream_t st);
+
+/* steps x (pauli_mlp_backward + pauli_mlp_adam_step with t = t0+1 .. t0+steps)
+ * in one call, enqueued on st; loss (device double, may be NULL) is that of
+ * the last step's forward pass. */
+int pauli_mlp_train(pauli_mlp *m, int batch, const float *x, const float *target, int steps, float lr, int t0,
+                    double *loss, pauli_stream_t st);
+
+int pauli_mlp_destroy(pauli_mlp *m);
+
 /* ------------------------------------------------------------------------- */
 /* launch-shape autotuning                                                    */
 /* ------------------------------------------------------------------------- */

@@ -58,6 +58,18 @@ SIGNATURES = {
     "pauli_expect": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "pauli_expect_noalloc": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "pauli_rotate": (_i32, [_vp, _vp, _dbl, _vp, _i32, _vp]),
+    "pauli_rotate_seq": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
+    "pauli_rotate_adjoint": (_i32, [_vp, _vp, _dbl, _vp, _vp, _i32, _vp, _vp]),
+    "pauli_vdot": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    "pauli_mlp_create": (_i32, [_i32, _i32, _i32, _i32, _vp]),
+    "pauli_mlp_num_params": (_i32, [_vp, _vp]),
+    "pauli_mlp_set_params": (_i32, [_vp, _vp]),
+    "pauli_mlp_get_params": (_i32, [_vp, _vp]),
+    "pauli_mlp_forward": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "pauli_mlp_backward": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "pauli_mlp_adam_step": (_i32, [_vp, C.c_float, _i32, _vp]),
+    "pauli_mlp_train": (_i32, [_vp, _i32, _vp, _vp, _i32, C.c_float, _i32, _vp, _vp]),
+    "pauli_mlp_destroy": (_i32, [_vp]),
     "pauli_status": (_i32, [_vp, _vp, _vp]),
     "pauli_tune": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp]),
     "pauli_set_launch_config": (_i32, [_vp, _vp, _i32, _vp]),
@@ -496,3 +508,137 @@ def rotate(G: PauliSum, s: Sector, theta: float, psi, stream=None):
     _check(lib().pauli_rotate(G._h, s._h, float(theta), C.c_void_p(psi.data_ptr()), _dtype_code(psi),
                               _stream_ptr(stream)))
     return psi
+
+
+def rotate_seq(Gs, s: Sector, thetas, psi, stream=None):
+    """psi <- prod_j exp(-i thetas[j] Gs[j]) psi in place, G_0 applied first."""
+    _check_state(psi, s.dim, "psi")
+    k = len(Gs)
+    if len(thetas) != k:
+        raise ValueError("Gs and thetas differ in length")
+    hs = (C.c_void_p * max(k, 1))(*[G._h.value for G in Gs])
+    th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(-1))
+    _check(lib().pauli_rotate_seq(hs, _np_ptr(th), k, s._h, C.c_void_p(psi.data_ptr()), _dtype_code(psi),
+                                  _stream_ptr(stream)))
+    return psi
+
+
+def rotate_adjoint(G: PauliSum, s: Sector, theta: float, phi, lam, out, stream=None):
+    """out[0:2] <- (Re, Im) <lam|G|phi> (device float64), then phi, lam <-
+    exp(-i theta G) phi, lam in place."""
+    _check_state(phi, s.dim, "phi")
+    _check_state(lam, s.dim, "lam")
+    _check(lib().pauli_rotate_adjoint(G._h, s._h, float(theta), C.c_void_p(phi.data_ptr()),
+                                      C.c_void_p(lam.data_ptr()), _dtype_code(phi), C.c_void_p(out.data_ptr()),
+                                      _stream_ptr(stream)))
+    return out
+
+
+def vdot(x, y, out=None, stream=None):
+    """<x|y> accumulated in FP64 on the device.  With out (a float64 device
+    tensor of 2) the result stays on the device; otherwise a Python complex."""
+    import torch
+    if x.dtype != y.dtype or x.numel() != y.numel():
+        raise TypeError("x and y must have the same dtype and size")
+    for v, nm in ((x, "x"), (y, "y")):
+        if not v.is_cuda or not v.is_contiguous() or v.data_ptr() % 16:
+            raise ValueError(f"{nm} must be a contiguous 16-byte aligned CUDA tensor")
+    res = out if out is not None else torch.empty(2, dtype=torch.float64, device=x.device)
+    if res.dtype != torch.float64 or res.numel() < 2 or not res.is_cuda:
+        raise ValueError("out must be a float64 CUDA tensor of 2 elements")
+    _check(lib().pauli_vdot(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), int(x.numel()), _dtype_code(x),
+                            C.c_void_p(res.data_ptr()), _stream_ptr(stream)))
+    if out is not None:
+        return out
+    r = res.cpu()
+    return complex(float(r[0]), float(r[1]))
+
+
+class MLP:
+    """Geometry -> ansatz-amplitude network of the learned warm start
+    (two tanh hidden layers; BF16 tensor-core products, FP32 master weights,
+    Adam).  Parameters are one FP32 vector: W1[in][hid], b1, W2[hid][hid], b2,
+    W3[hid][out], b3."""
+
+    def __init__(self, in_dim: int, hidden: int, out_dim: int, max_batch: int):
+        out = C.c_void_p()
+        _check(lib().pauli_mlp_create(int(in_dim), int(hidden), int(out_dim), int(max_batch), C.byref(out)))
+        self._h = out
+        self.in_dim, self.hidden, self.out_dim, self.max_batch = in_dim, hidden, out_dim, max_batch
+        n = C.c_int64()
+        _check(lib().pauli_mlp_num_params(self._h, C.byref(n)))
+        self.num_params = n.value
+
+    def shapes(self):
+        i, h, o = self.in_dim, self.hidden, self.out_dim
+        return [("W1", (i, h)), ("b1", (h,)), ("W2", (h, h)), ("b2", (h,)), ("W3", (h, o)), ("b3", (o,))]
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if p.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters, got {p.size}")
+        _check(lib().pauli_mlp_set_params(self._h, _np_ptr(p)))
+
+    def get_params(self):
+        p = np.zeros(self.num_params, dtype=np.float32)
+        _check(lib().pauli_mlp_get_params(self._h, _np_ptr(p)))
+        return p
+
+    def _check_batch(self, x, width, nm):
+        import torch
+        if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or x.dim() != 2 or x.shape[1] != width:
+            raise ValueError(f"{nm} must be a contiguous float32 CUDA tensor of shape (batch, {width})")
+        if not 1 <= x.shape[0] <= self.max_batch:
+            raise ValueError("batch size out of range")
+
+    def forward(self, x, stream=None):
+        import torch
+        self._check_batch(x, self.in_dim, "x")
+        y = torch.empty(x.shape[0], self.out_dim, dtype=torch.float32, device=x.device)
+        _check(lib().pauli_mlp_forward(self._h, int(x.shape[0]), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                       _stream_ptr(stream)))
+        return y
+
+    def backward(self, x, target, want_grads: bool = False, stream=None):
+        """Loss 1/(2B) sum (y - target)^2 as a float64 device tensor (and the
+        gradient vector when want_grads)."""
+        import torch
+        self._check_batch(x, self.in_dim, "x")
+        self._check_batch(target, self.out_dim, "target")
+        if target.shape[0] != x.shape[0]:
+            raise ValueError("x and target differ in batch size")
+        loss = torch.empty(1, dtype=torch.float64, device=x.device)
+        g = torch.empty(self.num_params, dtype=torch.float32, device=x.device) if want_grads else None
+        _check(lib().pauli_mlp_backward(self._h, int(x.shape[0]), C.c_void_p(x.data_ptr()),
+                                        C.c_void_p(target.data_ptr()), C.c_void_p(g.data_ptr() if g is not None else 0),
+                                        C.c_void_p(loss.data_ptr()), _stream_ptr(stream)))
+        return (loss, g) if want_grads else loss
+
+    def train(self, x, target, steps: int, lr: float, t0: int, stream=None):
+        """steps Adam steps (t = t0+1 ..) on (x, target) in one library call;
+        returns the last step's loss as a float64 device tensor."""
+        import torch
+        self._check_batch(x, self.in_dim, "x")
+        self._check_batch(target, self.out_dim, "target")
+        if target.shape[0] != x.shape[0]:
+            raise ValueError("x and target differ in batch size")
+        loss = torch.full((1,), float("nan"), dtype=torch.float64, device=x.device)
+        _check(lib().pauli_mlp_train(self._h, int(x.shape[0]), C.c_void_p(x.data_ptr()),
+                                     C.c_void_p(target.data_ptr()), int(steps), C.c_float(lr), int(t0),
+                                     C.c_void_p(loss.data_ptr()), _stream_ptr(stream)))
+        return loss
+
+    def adam_step(self, lr: float, t: int, stream=None):
+        _check(lib().pauli_mlp_adam_step(self._h, C.c_float(lr), int(t), _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            if _lib is not None:
+                lib().pauli_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

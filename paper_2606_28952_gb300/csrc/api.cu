@@ -512,6 +512,28 @@ int pauli_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, i
     });
 }
 
+int pauli_rotate_adjoint(pauli_sum *G, const pauli_sector *s, double theta, void *phi, void *lam, int dtype,
+                         double *result, pauli_stream_t st) {
+    return guarded([&] {
+        check_sum(G);
+        check_sector(s);
+        check_dtype(dtype);
+        PS_CHECK(G->n == s->v.n, PAULI_EINVAL, "generator and sector have different qubit counts");
+        PS_CHECK(std::isfinite(theta), PAULI_EINVAL, "theta must be finite");
+        check_state_ptr(phi, dtype, "phi");
+        check_state_ptr(lam, dtype, "lam");
+        PS_CHECK(phi != lam, PAULI_EINVAL, "phi and lam must be different vectors");
+        PS_CHECK(result != nullptr, PAULI_EINVAL, "result is NULL");
+        PS_CHECK(G->m == 0 || G->G == 1, PAULI_EINVAL, "rotation generator must have exactly one X mask");
+        PS_CHECK(G->hermitian, PAULI_ENOTHERMITIAN, "rotation generator is not Hermitian");
+        if (G->m == 0) {
+            PS_CUDA(cudaMemsetAsync(result, 0, 2 * sizeof(double), (cudaStream_t)st));
+            return;
+        }
+        launch_rotate_adjoint(G, s->v, theta, phi, lam, dtype, result, (cudaStream_t)st);
+    });
+}
+
 int pauli_status(pauli_sum *H, pauli_stream_t st, int *code) {
     return guarded([&] {
         check_sum(H);

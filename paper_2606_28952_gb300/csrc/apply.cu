@@ -115,6 +115,129 @@ k_rotate(SectorView v, Geom geo, int64_t m, uint64_t x, const uint64_t *__restri
     psi[sidx] = nb;
 }
 
+// Fused step of the adjoint gradient sweep over a product ansatz: each
+// lower-index thread of a pair {t, s = t XOR x} adds its part of
+// <lam|G|phi> = sum_t conj(lam_t) f_t phi_s (f_s = conj(f_t)) from the input
+// values, then rotates both phi and lam by exp(-i theta G).  (The matrix
+// element is the same before and after, since G commutes with its own
+// exponential.)  Fixed grid; block b handles work units b, b + gridDim.x, ...
+// and writes its FP64 sum to partials[4b..4b+1], so the result is
+// reproducible.
+template <typename R, bool FULL>
+__global__ void __launch_bounds__(kThreads)
+k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const uint64_t *__restrict__ z,
+             const double2 *__restrict__ c, R theta, typename Cx<R>::T *phi, typename Cx<R>::T *lam,
+             double *partials, int *status) {
+    using C2 = typename Cx<R>::T;
+    __shared__ uint64_t sm_z[kRotChunk];
+    __shared__ C2 sm_c[kRotChunk];
+    __shared__ double red[2][kThreads / 32];
+    const int tid = threadIdx.x;
+    const uint32_t xlo = (uint32_t)(x & ((1ull << v.n_lo) - 1ull));
+    const uint32_t xhi = (uint32_t)(x >> v.n_lo);
+    double mr = 0.0, mi = 0.0;
+    for (int64_t work = blockIdx.x; work < nwork; work += gridDim.x) {
+        const RowCtx rc = decode_row<FULL>(v, geo, work);
+        const int64_t col = rc.c0 + tid;
+        const bool act = col < rc.dlo;
+        uint32_t tlo = 0;
+        if (act) tlo = FULL ? (uint32_t)col : __ldg(v.list_lo + v.list_lo_off[v.klo[rc.blk]] + col);
+        const uint32_t shi = rc.thi ^ xhi, slo = tlo ^ xlo;
+        const uint64_t s = (uint64_t)slo | ((uint64_t)shi << v.n_lo);
+        R fr = R(0), fi = R(0);
+        for (int64_t k0 = 0; k0 < m; k0 += kRotChunk) {
+            const int cnt = (m - k0 < kRotChunk) ? (int)(m - k0) : kRotChunk;
+            __syncthreads();
+            if (tid < cnt) {
+                sm_z[tid] = z[k0 + tid];
+                const double2 cc = c[k0 + tid];
+                C2 cv;
+                cv.x = (R)cc.x;
+                cv.y = (R)cc.y;
+                sm_c[tid] = cv;
+            }
+            __syncthreads();
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t par = __popcll(sm_z[k] & s);
+                fr += flip(sm_c[k].x, par);
+                fi += flip(sm_c[k].y, par);
+            }
+        }
+        if (!act) continue;
+        int64_t sidx;
+        if (FULL) {
+            sidx = (int64_t)s;
+        } else {
+            const int bb = v.blk_of_khi[__popc(shi)];
+            if (bb < 0 || __popc(slo) != v.klo[bb]) {
+                if (fr != R(0) || fi != R(0)) atomicCAS(status, 0, (int)PAULI_ESECTOR);
+                continue;
+            }
+            sidx = v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb] + (int64_t)__ldg(v.rank_lo + slo);
+        }
+        const int64_t tidx = rc.own_base + col;
+        if (x == 0) {
+            const C2 a = phi[tidx], la = lam[tidx];
+            mr += (double)fr * ((double)la.x * a.x + (double)la.y * a.y);
+            mi += (double)fr * ((double)la.x * a.y - (double)la.y * a.x);
+            R sn, cs;
+            sincos_r<R>(theta * fr, &sn, &cs);
+            C2 o, lo;
+            o.x = cs * a.x + sn * a.y;
+            o.y = cs * a.y - sn * a.x;
+            lo.x = cs * la.x + sn * la.y;
+            lo.y = cs * la.y - sn * la.x;
+            phi[tidx] = o;
+            lam[tidx] = lo;
+            continue;
+        }
+        if (tidx >= sidx) continue;
+        const R mag = sqrt(fr * fr + fi * fi);
+        if (mag == R(0)) continue;
+        const C2 a = phi[tidx], b = phi[sidx], la = lam[tidx], lb = lam[sidx];
+        // conj(la) f b + conj(lb) conj(f) a
+        {
+            const double pr = (double)fr * b.x - (double)fi * b.y, pi = (double)fr * b.y + (double)fi * b.x;
+            const double qr = (double)fr * a.x + (double)fi * a.y, qi = (double)fr * a.y - (double)fi * a.x;
+            mr += (double)la.x * pr + (double)la.y * pi + (double)lb.x * qr + (double)lb.y * qi;
+            mi += (double)la.x * pi - (double)la.y * pr + (double)lb.x * qi - (double)lb.y * qr;
+        }
+        R sn, cs;
+        sincos_r<R>(theta * mag, &sn, &cs);
+        const R q = sn / mag;
+        auto rot = [&](const C2 &u, const C2 &w, C2 &nu, C2 &nw) {
+            const R wr = fr * w.x - fi * w.y, wi = fr * w.y + fi * w.x;
+            const R ur = fr * u.x + fi * u.y, ui = fr * u.y - fi * u.x;
+            nu.x = cs * u.x + q * wi;
+            nu.y = cs * u.y - q * wr;
+            nw.x = cs * w.x + q * ui;
+            nw.y = cs * w.y - q * ur;
+        };
+        C2 na, nb, nla, nlb;
+        rot(a, b, na, nb);
+        rot(la, lb, nla, nlb);
+        phi[tidx] = na;
+        phi[sidx] = nb;
+        lam[tidx] = nla;
+        lam[sidx] = nlb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mr += __shfl_down_sync(0xffffffffu, mr, o);
+        mi += __shfl_down_sync(0xffffffffu, mi, o);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = mr;
+        red[1][tid >> 5] = mi;
+    }
+    __syncthreads();
+    if (tid < 2) {
+        double acc = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) acc += red[tid][w];
+        partials[(int64_t)blockIdx.x * 4 + tid] = acc;
+    }
+}
+
 }  // namespace
 
 // 227 KB of shared memory per block on sm_103a, less room for the kernel's static arrays
@@ -242,10 +365,43 @@ void launch_reduce(const double *partials, int64_t nparts, double *result, cudaS
     k_reduce<<<1, 1024, 0, st>>>(partials, nparts, result);
     PS_LAUNCH_CHECK();
 }
+// X mask of a single-group operator, read back from the device once
+static uint64_t group_mask0(pauli_sum *G) {
+    if (!G->gx0_known) {
+        uint64_t x = 0;
+        if (G->G == 1) PS_CUDA(cudaMemcpy(&x, G->gx, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        G->gx0_host = x;
+        G->gx0_known = true;
+    }
+    return G->gx0_host;
+}
+
+void launch_rotate_adjoint(pauli_sum *G, const SectorView &v, double theta, void *phi, void *lam, int dtype,
+                           double *result, cudaStream_t st) {
+    const uint64_t x = group_mask0(G);
+    const Geom geo = make_geom(v, kThreads);
+    const int64_t nwork = geo.cta_off[v.nblk];
+    DotScratch &d = dot_scratch();
+    const unsigned grid = (unsigned)(nwork < d.blocks ? (nwork > 0 ? nwork : 1) : d.blocks);
+    const bool full = v.kind == PAULI_SECTOR_FULL;
+    if (dtype == PAULI_C64) {
+        auto *a = static_cast<float2 *>(phi);
+        auto *b = static_cast<float2 *>(lam);
+        if (full) k_rotate_adj<float, true><<<grid, kThreads, 0, st>>>(v, geo, nwork, G->m, x, G->z, G->c, (float)theta, a, b, d.partials, G->status);
+        else k_rotate_adj<float, false><<<grid, kThreads, 0, st>>>(v, geo, nwork, G->m, x, G->z, G->c, (float)theta, a, b, d.partials, G->status);
+    } else {
+        auto *a = static_cast<double2 *>(phi);
+        auto *b = static_cast<double2 *>(lam);
+        if (full) k_rotate_adj<double, true><<<grid, kThreads, 0, st>>>(v, geo, nwork, G->m, x, G->z, G->c, theta, a, b, d.partials, G->status);
+        else k_rotate_adj<double, false><<<grid, kThreads, 0, st>>>(v, geo, nwork, G->m, x, G->z, G->c, theta, a, b, d.partials, G->status);
+    }
+    PS_LAUNCH_CHECK();
+    launch_reduce2(d.partials, grid, result, st);
+}
+
 void launch_rotate(pauli_sum *G, const SectorView &v, double theta, void *psi, int dtype,
                    cudaStream_t st) {
-    uint64_t x = 0;
-    if (G->G == 1) PS_CUDA(cudaMemcpy(&x, G->gx, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    const uint64_t x = group_mask0(G);
     const Geom geo = make_geom(v, kThreads);
     const int64_t nct = geo.cta_off[v.nblk];
     if (nct == 0) return;

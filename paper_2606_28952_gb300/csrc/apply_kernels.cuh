@@ -155,8 +155,10 @@ template <typename R>
 struct Smem {
     using C2 = typename Cx<R>::T;
     // byte offsets inside one buffer
+    // the low parts of the x = 0 group's coefficients exist on the FP32 path only
+    static constexpr size_t kLoBytes = sizeof(R) == 4 ? sizeof(float2) : 0;
     static __host__ __device__ size_t buf_bytes(int rw) {
-        return (size_t)rw * sizeof(C2) + (size_t)kSegCap * (sizeof(C2) + sizeof(float2) + 4) +
+        return (size_t)rw * sizeof(C2) + (size_t)kSegCap * (sizeof(C2) + kLoBytes + 4) +
                (size_t)kItemCap * sizeof(int4);
     }
 };
@@ -169,14 +171,14 @@ struct Buf {
     using C2 = typename Cx<R>::T;
     C2 *row;
     C2 *a;
-    float2 *alo;   // low parts of the x = 0 group's coefficients (FP32 path)
+    float2 *alo;   // low parts of the x = 0 group's coefficients (FP32 path only; no storage for FP64)
     int4 *item;    // {x_lo, seg begin, seg end, diagonal}
     uint32_t *z;
     __device__ Buf(char *base, int rw) {
         row = reinterpret_cast<C2 *>(base);
         a = reinterpret_cast<C2 *>(base + (size_t)rw * sizeof(C2));
         alo = reinterpret_cast<float2 *>(reinterpret_cast<char *>(a) + (size_t)kSegCap * sizeof(C2));
-        item = reinterpret_cast<int4 *>(reinterpret_cast<char *>(alo) + (size_t)kSegCap * sizeof(float2));
+        item = reinterpret_cast<int4 *>(reinterpret_cast<char *>(alo) + (size_t)kSegCap * Smem<R>::kLoBytes);
         z = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(item) + (size_t)kItemCap * sizeof(int4));
     }
 };
@@ -259,7 +261,7 @@ __device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &
             a.y = ai;
         }
         B.a[s - sbase] = a;
-        B.alo[s - sbase] = lo;
+        if (sizeof(R) == 4) B.alo[s - sbase] = lo;
         B.z[s - sbase] = __ldg(p.s_zlo + s);
     }
     if (KIND == KBLKN && tid == 0) *klo_req = klo;

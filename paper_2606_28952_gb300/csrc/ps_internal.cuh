@@ -171,6 +171,8 @@ struct pauli_sum {
     uint64_t *gx = nullptr;               // [G]
     int64_t *gstart = nullptr;            // [G+1]
     int *status = nullptr;                // device status word
+    uint64_t gx0_host = 0;                // gx[0] read back once (single-group rotations)
+    bool gx0_known = false;
     ps::Plan plans[4];
     int nplans = 0;
 };
@@ -243,4 +245,16 @@ int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow
 int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype, const LaunchChoice *force = nullptr);
 void launch_rotate(pauli_sum *G, const SectorView &v, double theta, void *psi, int dtype,
                    cudaStream_t st);
+// <lam|G|phi> into result[0..1] (device), then phi, lam <- exp(-i theta G) phi, lam
+void launch_rotate_adjoint(pauli_sum *G, const SectorView &v, double theta, void *phi, void *lam, int dtype,
+                           double *result, cudaStream_t st);
+
+// linalg.cu: per-device scratch of FP64 partial sums shared by the reductions
+// that run on a fixed grid (pauli_vdot, pauli_rotate_adjoint)
+struct DotScratch {
+    double *partials = nullptr;  // [blocks][4]
+    int blocks = 0;
+};
+DotScratch &dot_scratch();
+void launch_reduce2(const double *partials, int64_t nparts, double *result, cudaStream_t st);
 }  // namespace ps
