@@ -135,7 +135,7 @@ k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const
     const int tid = threadIdx.x;
     const uint32_t xlo = (uint32_t)(x & ((1ull << v.n_lo) - 1ull));
     const uint32_t xhi = (uint32_t)(x >> v.n_lo);
-    double mr = 0.0, mi = 0.0;
+    DotAcc<R> dot;
     for (int64_t work = blockIdx.x; work < nwork; work += gridDim.x) {
         const RowCtx rc = decode_row<FULL>(v, geo, work);
         const int64_t col = rc.c0 + tid;
@@ -178,8 +178,10 @@ k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const
         const int64_t tidx = rc.own_base + col;
         if (x == 0) {
             const C2 a = phi[tidx], la = lam[tidx];
-            mr += (double)fr * ((double)la.x * a.x + (double)la.y * a.y);
-            mi += (double)fr * ((double)la.x * a.y - (double)la.y * a.x);
+            C2 fa;
+            fa.x = fr * a.x;
+            fa.y = fr * a.y;
+            dot.add(la, fa);
             R sn, cs;
             sincos_r<R>(theta * fr, &sn, &cs);
             C2 o, lo;
@@ -197,10 +199,13 @@ k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const
         const C2 a = phi[tidx], b = phi[sidx], la = lam[tidx], lb = lam[sidx];
         // conj(la) f b + conj(lb) conj(f) a
         {
-            const double pr = (double)fr * b.x - (double)fi * b.y, pi = (double)fr * b.y + (double)fi * b.x;
-            const double qr = (double)fr * a.x + (double)fi * a.y, qi = (double)fr * a.y - (double)fi * a.x;
-            mr += (double)la.x * pr + (double)la.y * pi + (double)lb.x * qr + (double)lb.y * qi;
-            mi += (double)la.x * pi - (double)la.y * pr + (double)lb.x * qi - (double)lb.y * qr;
+            C2 fb, fa;
+            fb.x = fr * b.x - fi * b.y;
+            fb.y = fr * b.y + fi * b.x;
+            fa.x = fr * a.x + fi * a.y;
+            fa.y = fr * a.y - fi * a.x;
+            dot.add(la, fb);
+            dot.add(lb, fa);
         }
         R sn, cs;
         sincos_r<R>(theta * mag, &sn, &cs);
@@ -221,6 +226,7 @@ k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const
         lam[tidx] = nla;
         lam[sidx] = nlb;
     }
+    double mr = dot.get_re(), mi = dot.get_im();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mr += __shfl_down_sync(0xffffffffu, mr, o);

@@ -134,6 +134,78 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Per-thread sum of conj(x) y: FP64 on the FP64 path; on the FP32 path exact
+// FP32 product splits summed with TwoSum, converted to FP64 once (as ExpAcc).
+template <typename R> struct DotAcc;
+template <> struct DotAcc<double> {
+    double re = 0.0, im = 0.0;
+    __device__ __forceinline__ void add(double2 x, double2 y) {
+        re += x.x * y.x + x.y * y.y;
+        im += x.x * y.y - x.y * y.x;
+    }
+    __device__ __forceinline__ double get_re() const { return re; }
+    __device__ __forceinline__ double get_im() const { return im; }
+};
+template <> struct DotAcc<float> {
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    __device__ __forceinline__ static void prod(float &s, float &c, float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        float t, err;
+        two_sum(s, p, t, err);
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void add(float2 x, float2 y) {
+        prod(sr, cr, x.x, y.x);
+        prod(sr, cr, x.y, y.y);
+        prod(si, ci, x.x, y.y);
+        prod(si, ci, -x.y, y.x);
+    }
+    __device__ __forceinline__ double get_re() const { return (double)sr + (double)cr; }
+    __device__ __forceinline__ double get_im() const { return (double)si + (double)ci; }
+};
+
+// Expectation partials of one thread's targets: {Re <psi|H psi>, Im, ||H psi||^2,
+// <psi|psi>}.  FP64 path: FP64 products and sums.  FP32 path: every product is
+// split exactly into FP32 hi + lo parts (FMA) and summed with TwoSum, so the
+// few terms of a thread lose nothing; each pair becomes one FP64 number when
+// the thread's partials enter the FP64 block reduction.  (FP64 arithmetic runs
+// at a small fraction of the FP32 rate on this GPU.)
+template <typename R> struct ExpAcc;
+template <> struct ExpAcc<double> {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    __device__ __forceinline__ void add(double2 ps, double hr, double hi) {
+        s[0] += ps.x * hr + ps.y * hi;
+        s[1] += ps.x * hi - ps.y * hr;
+        s[2] += hr * hr + hi * hi;
+        s[3] += ps.x * ps.x + ps.y * ps.y;
+    }
+    __device__ __forceinline__ double get(int k) const { return s[k]; }
+};
+template <> struct ExpAcc<float> {
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ void prod(int k, float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        float t, err;
+        two_sum(s[k], p, t, err);
+        s[k] = t;
+        c[k] = __fadd_rn(c[k], __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void add(float2 ps, float hr, float hi) {
+        prod(0, ps.x, hr);
+        prod(0, ps.y, hi);
+        prod(1, ps.x, hi);
+        prod(1, -ps.y, hr);
+        prod(2, hr, hr);
+        prod(2, hi, hi);
+        prod(3, ps.x, ps.x);
+        prod(3, ps.y, ps.y);
+    }
+    __device__ __forceinline__ double get(int k) const { return (double)s[k] + (double)c[k]; }
+};
+
 // KFULL: full space; KBLK1 / KBLKN: one / several product blocks, source rows
 // staged by bit pattern (2^n_lo slots, zeros outside the block); KBLKR: one
 // product block, source rows staged densely by rank and found through a rank
@@ -475,7 +547,7 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
     }
 
     // epilogue: store and / or FP64 reductions
-    double er = 0.0, ei = 0.0, h2 = 0.0, p2 = 0.0;
+    ExpAcc<R> ea;
 #pragma unroll
     for (int j = 0; j < TPT; ++j) {
         if (!act[j]) continue;
@@ -487,17 +559,10 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
             // split launches write partial sums to slice `split` of the scratch
             out[(flags & 4) ? (int64_t)rc.split * v.dim + idx : idx] = o;
         }
-        if (flags & 2) {
-            const C2 ps = psi[idx];
-            const double pr = (double)ps.x, pi = (double)ps.y;
-            const double hr = (double)accr[j], hi = (double)acci[j];
-            er += pr * hr + pi * hi;
-            ei += pr * hi - pi * hr;
-            h2 += hr * hr + hi * hi;
-            p2 += pr * pr + pi * pi;
-        }
+        if (flags & 2) ea.add(psi[idx], accr[j], acci[j]);
     }
     if (flags & 2) {
+        double er = ea.get(0), ei = ea.get(1), h2 = ea.get(2), p2 = ea.get(3);
         __shared__ double red[4][kThreads / 32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -781,7 +846,7 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
         }
     }
     // epilogue (same contract as k_apply)
-    double er = 0.0, ei = 0.0, h2 = 0.0, p2 = 0.0;
+    ExpAcc<R> ea;
 #pragma unroll
     for (int j = 0; j < TPT; ++j) {
         if (!act[j]) continue;
@@ -792,17 +857,10 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
             o.y = acci[j];
             out[idx] = o;
         }
-        if (flags & 2) {
-            const C2 ps = psi[idx];
-            const double pr = (double)ps.x, pi = (double)ps.y;
-            const double hr = (double)accr[j], hi = (double)acci[j];
-            er += pr * hr + pi * hi;
-            ei += pr * hi - pi * hr;
-            h2 += hr * hr + hi * hi;
-            p2 += pr * pr + pi * pi;
-        }
+        if (flags & 2) ea.add(psi[idx], accr[j], acci[j]);
     }
     if (flags & 2) {
+        double er = ea.get(0), ei = ea.get(1), h2 = ea.get(2), p2 = ea.get(3);
         __shared__ double red[4][kThreads / 32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -835,7 +893,7 @@ k_combine(int nsplit, int64_t dim, const typename Cx<R>::T *__restrict__ part, c
           typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
     using C2 = typename Cx<R>::T;
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    double er = 0.0, ei = 0.0, h2 = 0.0, p2 = 0.0;
+    ExpAcc<R> ea;
     if (i < dim) {
         C2 s = part[i];
         for (int k = 1; k < nsplit; ++k) {
@@ -844,16 +902,10 @@ k_combine(int nsplit, int64_t dim, const typename Cx<R>::T *__restrict__ part, c
             s.y += t.y;
         }
         if (flags & 1) out[i] = s;
-        if (flags & 2) {
-            const C2 ps = psi[i];
-            const double pr = (double)ps.x, pi = (double)ps.y, hr = (double)s.x, hi = (double)s.y;
-            er = pr * hr + pi * hi;
-            ei = pr * hi - pi * hr;
-            h2 = hr * hr + hi * hi;
-            p2 = pr * pr + pi * pi;
-        }
+        if (flags & 2) ea.add(psi[i], s.x, s.y);
     }
     if (flags & 2) {
+        double er = ea.get(0), ei = ea.get(1), h2 = ea.get(2), p2 = ea.get(3);
         __shared__ double red[4][kThreads / 32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

@@ -48,16 +48,41 @@ __device__ __forceinline__ void block_sum_store(double v, double *partials) {
     }
 }
 
-// partial sums of ||x||^2 (FP64)
+// Per-thread sum of |x_i|^2.  FP64 vectors: FP64.  FP32 vectors: each square
+// split exactly into FP32 hi + lo (FMA) and added with TwoSum (compensated
+// summation, error ~ one FP32 rounding of the thread's total), converted to
+// FP64 for the block and grid reduction; FP64 arithmetic is slow on this GPU.
+template <typename R> struct NormAcc;
+template <> struct NormAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double2 v) { s += v.x * v.x + v.y * v.y; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct NormAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void sq(float a) {
+        const float p = __fmul_rn(a, a);
+        const float e = __fmaf_rn(a, a, -p);
+        float t, err;
+        two_sum(s, p, t, err);
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void add(float2 v) {
+        sq(v.x);
+        sq(v.y);
+    }
+    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+// partial sums of ||x||^2
 template <typename R>
 __global__ void __launch_bounds__(kVecThreads) k_norm2(const typename Cx<R>::T *__restrict__ x, int64_t n,
                                                        double *partials) {
-    double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads) {
-        const typename Cx<R>::T v = x[i];
-        s += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-    }
-    block_sum_store<R>(s, partials);
+    NormAcc<R> acc;
+    for (int64_t i = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads)
+        acc.add(x[i]);
+    block_sum_store<R>(acc.get(), partials);
 }
 
 // y = x / sqrt(sc->red[0]) (zero if the norm vanished); records the norm in *beta_out
@@ -88,7 +113,7 @@ k_lanczos_update(typename Cx<R>::T *__restrict__ w, const typename Cx<R>::T *__r
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->alpha[j] = alpha;
     const R a = (R)alpha;
     const R b = vjm1 ? (R)sc->beta[j] : R(0);
-    double s = 0.0;
+    NormAcc<R> acc;
     for (int64_t i = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads) {
         typename Cx<R>::T x = w[i];
         const typename Cx<R>::T v = vj[i];
@@ -100,9 +125,9 @@ k_lanczos_update(typename Cx<R>::T *__restrict__ w, const typename Cx<R>::T *__r
             x.y -= b * u.y;
         }
         w[i] = x;
-        s += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+        acc.add(x);
     }
-    block_sum_store<R>(s, partials);
+    block_sum_store<R>(acc.get(), partials);
 }
 
 // One CTA: eigen-decomposition of T_m by cyclic Jacobi rotations (FP64), then
@@ -164,28 +189,65 @@ __global__ void k_tridiag_expm(KrylovScalars *sc, int m, double dt) {
     }
 }
 
-// psi = sum_j c_j v_j
+// psi = sum_j c_j v_j.  FP64 vectors: FP64.  FP32 vectors: each c_j split
+// once per block into FP32 hi + lo parts; per element the products are split
+// exactly (FMA) and summed with TwoSum compensation, so the sum is about
+// FP64-accurate before its final rounding to FP32.
+template <typename R> struct CombineAcc;
+template <> struct CombineAcc<double> {
+    double re = 0.0, im = 0.0;
+    __device__ __forceinline__ void add(const float4 &, double cr, double ci, double2 v) {
+        re += cr * v.x - ci * v.y;
+        im += cr * v.y + ci * v.x;
+    }
+    __device__ __forceinline__ double2 get() const { return make_double2(re, im); }
+};
+template <> struct CombineAcc<float> {
+    float sr = 0.f, er = 0.f, si = 0.f, ei = 0.f;
+    __device__ __forceinline__ static void acc(float &s, float &c, float p) {
+        float t, err;
+        two_sum(s, p, t, err);
+        s = t;
+        c = __fadd_rn(c, err);
+    }
+    // c4 = {Re c hi, Re c lo, Im c hi, Im c lo}
+    __device__ __forceinline__ void add(const float4 &c4, double, double, float2 v) {
+        const float p1 = __fmul_rn(c4.x, v.x), q1 = __fmaf_rn(c4.x, v.x, -p1);
+        const float p2 = __fmul_rn(c4.z, v.y), q2 = __fmaf_rn(c4.z, v.y, -p2);
+        const float p3 = __fmul_rn(c4.x, v.y), q3 = __fmaf_rn(c4.x, v.y, -p3);
+        const float p4 = __fmul_rn(c4.z, v.x), q4 = __fmaf_rn(c4.z, v.x, -p4);
+        acc(sr, er, p1);
+        acc(sr, er, -p2);
+        er = __fadd_rn(er, (q1 - q2) + (c4.y * v.x - c4.w * v.y));
+        acc(si, ei, p3);
+        acc(si, ei, p4);
+        ei = __fadd_rn(ei, (q3 + q4) + (c4.y * v.y + c4.w * v.x));
+    }
+    __device__ __forceinline__ float2 get() const { return make_float2(sr + er, si + ei); }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(kVecThreads) k_krylov_combine(const typename Cx<R>::T *__restrict__ V, int64_t n,
                                                                 int m, const KrylovScalars *sc,
                                                                 typename Cx<R>::T *__restrict__ psi) {
     __shared__ double cr[kMaxKrylov], ci[kMaxKrylov];
+    __shared__ float4 c4[kMaxKrylov];
     if (threadIdx.x < m) {
-        cr[threadIdx.x] = sc->cre[threadIdx.x];
-        ci[threadIdx.x] = sc->cim[threadIdx.x];
+        const double a = sc->cre[threadIdx.x], b = sc->cim[threadIdx.x];
+        cr[threadIdx.x] = a;
+        ci[threadIdx.x] = b;
+        const float ah = (float)a, bh = (float)b;
+        c4[threadIdx.x] = make_float4(ah, (float)(a - (double)ah), bh, (float)(b - (double)bh));
     }
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads) {
-        double re = 0.0, im = 0.0;
-        for (int j = 0; j < m; ++j) {
-            const typename Cx<R>::T v = V[(int64_t)j * n + i];
-            re += cr[j] * (double)v.x - ci[j] * (double)v.y;
-            im += cr[j] * (double)v.y + ci[j] * (double)v.x;
-        }
-        typename Cx<R>::T o;
-        o.x = (R)re;
-        o.y = (R)im;
-        psi[i] = o;
+        CombineAcc<R> acc;
+        for (int j = 0; j < m; ++j) acc.add(c4[j], cr[j], ci[j], V[(int64_t)j * n + i]);
+        const auto o = acc.get();
+        typename Cx<R>::T r;
+        r.x = (R)o.x;
+        r.y = (R)o.y;
+        psi[i] = r;
     }
 }
 

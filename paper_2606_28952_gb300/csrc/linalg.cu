@@ -10,18 +10,15 @@ namespace {
 
 constexpr int kDotThreads = 256;
 
-// partial sums of <x|y> = sum conj(x_i) y_i in FP64 (4-wide slots for k_reduce4)
+// partial sums of <x|y> = sum conj(x_i) y_i (per-thread DotAcc, FP64 across threads)
 template <typename R>
 __global__ void __launch_bounds__(kDotThreads) k_vdot(const typename Cx<R>::T *__restrict__ x,
                                                       const typename Cx<R>::T *__restrict__ y, int64_t n,
                                                       double *partials) {
-    double re = 0.0, im = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kDotThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDotThreads) {
-        const typename Cx<R>::T a = x[i], b = y[i];
-        const double ar = a.x, ai = a.y, br = b.x, bi = b.y;
-        re += ar * br + ai * bi;
-        im += ar * bi - ai * br;
-    }
+    DotAcc<R> dot;
+    for (int64_t i = (int64_t)blockIdx.x * kDotThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDotThreads)
+        dot.add(x[i], y[i]);
+    double re = dot.get_re(), im = dot.get_im();
     __shared__ double red[2][kDotThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
