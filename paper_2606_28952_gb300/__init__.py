@@ -400,6 +400,13 @@ def tune(H: PauliSum, s: Sector, dtype=None, reps: int = 5, cache: str | None = 
     return dict(out, cached=False)
 
 
+def set_launch_config(H: PauliSum, s: Sector, dtype, cfg: "LaunchConfig"):
+    """Install a launch shape for (H, s, dtype) (pauli_set_launch_config)."""
+    import torch
+    code = C64 if dtype in (None, torch.complex64) else C128
+    _check(lib().pauli_set_launch_config(H._h, s._h, code, C.byref(cfg)))
+
+
 def launch_config(H: PauliSum, s: Sector, dtype=None) -> dict:
     import torch
     code = C64 if dtype in (None, torch.complex64) else C128

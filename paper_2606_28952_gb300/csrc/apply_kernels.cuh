@@ -74,6 +74,10 @@ struct PlanDev {
     const uint32_t *t_zhi;
     const double2 *t_c64;
     const float2 *t_c32;
+    const double2 *diag_tab64;  // null: no diagonal table for this split
+    const float2 *diag_tab32;
+    const int32_t *diag_rest;
+    int32_t n_diag_rest;
 };
 
 template <typename R> __device__ __forceinline__ typename Cx<R>::T coef(const PlanDev &p, int t);
@@ -681,11 +685,11 @@ struct DItem {
     int klo;        // popcount required of the source column, -1: row invalid
     int s0, s1;     // segment range (the first is skipped into f0 when its z_lo == 0)
     int diag;       // x = 0 group on the FP32 path: compensated sum
-    int pad;
+    int x0;         // x = 0 group (either path)
 };
 
 template <typename R, int KIND, bool REALH, int TPT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
                typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
     using C2 = typename Cx<R>::T;
@@ -704,7 +708,7 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
         e.s0 = s0;
         e.s1 = s1;
         e.diag = (sizeof(R) == 4 && s0 < p.nseg_diag) ? 1 : 0;
-        e.pad = 0;
+        e.x0 = s0 < p.nseg_diag ? 1 : 0;
         if (KIND == KFULL) {
             e.klo = 0;
             e.base = (int64_t)shi << v.n_lo;
@@ -715,10 +719,14 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
         }
         sm_it[it] = e;
     }
-    // phase 1b: one thread per segment folds the row's high-half phases
+    // phase 1b: one thread per segment folds the row's high-half phases (with
+    // a diagonal table, the tabulated z_hi = 0 term of a diagonal segment is left out)
+    const bool use_tab = p.diag_tab64 != nullptr;
     for (int s = tid; s < p.S; s += kThreads) {
         const uint32_t shi = rc.thi ^ __ldg(p.s_xhi + s);
-        const int t0 = __ldg(p.s_t0 + s), t1 = __ldg(p.s_t0 + s + 1);
+        int t0 = __ldg(p.s_t0 + s);
+        const int t1 = __ldg(p.s_t0 + s + 1);
+        if (use_tab && s < p.nseg_diag && __ldg(p.t_zhi + t0) == 0u) ++t0;
         C2 a;
         float2 lo = make_float2(0.f, 0.f);
         if (sizeof(R) == 4 && s < p.nseg_diag) {
@@ -784,6 +792,76 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
             }
         }
         R fr[TPT], fi[TPT];
+        if (use_tab && e.x0) {
+            // x = 0 group: table of the z_hi = 0 terms plus the remaining segments
+            if (e.s0 != 0) continue;  // later items of a split diagonal group are covered here
+            const uint32_t ntab = 1u << v.n_lo;
+            if (sizeof(R) == 4) {
+                R er[TPT], ei[TPT];
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) {
+                    const float2 h = __ldg(p.diag_tab32 + s[j]);
+                    const float2 l = __ldg(p.diag_tab32 + ntab + s[j]);
+                    fr[j] = (R)h.x;
+                    fi[j] = (R)h.y;
+                    er[j] = (R)l.x;
+                    ei[j] = (R)l.y;
+                }
+                for (int r = 0; r < p.n_diag_rest; ++r) {
+                    const int sgr = __ldg(p.diag_rest + r);
+                    const uint32_t z = sm_z[sgr];
+                    const C2 a = sm_a[sgr];
+                    const float2 l = sm_lo[sgr];
+#pragma unroll
+                    for (int j = 0; j < TPT; ++j) {
+                        const uint32_t par = __popc(z & s[j]);
+                        float t, err;
+                        two_sum(fr[j], flip((float)a.x, par), t, err);
+                        fr[j] = t;
+                        er[j] += err + flip(l.x, par);
+                        if (!REALH) {
+                            two_sum(fi[j], flip((float)a.y, par), t, err);
+                            fi[j] = t;
+                            ei[j] += err + flip(l.y, par);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) {
+                    fr[j] += er[j];
+                    fi[j] += ei[j];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) {
+                    const double2 h = __ldg(p.diag_tab64 + s[j]);
+                    fr[j] = (R)h.x;
+                    fi[j] = (R)h.y;
+                }
+                for (int r = 0; r < p.n_diag_rest; ++r) {
+                    const int sgr = __ldg(p.diag_rest + r);
+                    const uint32_t z = sm_z[sgr];
+                    const C2 a = sm_a[sgr];
+#pragma unroll
+                    for (int j = 0; j < TPT; ++j) {
+                        const uint32_t par = __popc(z & s[j]);
+                        fr[j] += flip(a.x, par);
+                        if (!REALH) fi[j] += flip(a.y, par);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                if (REALH) {
+                    accr[j] += fr[j] * amp[j].x;
+                    acci[j] += fr[j] * amp[j].y;
+                } else {
+                    accr[j] += fr[j] * amp[j].x - fi[j] * amp[j].y;
+                    acci[j] += fr[j] * amp[j].y + fi[j] * amp[j].x;
+                }
+            }
+            continue;
+        }
         int sg = e.s0;
         const bool zfirst = sm_z[e.s0] == 0;
 #pragma unroll
@@ -973,6 +1051,10 @@ PlanDev plan_dev(const Plan &p) {
     d.t_zhi = p.t_zhi;
     d.t_c64 = p.t_c64;
     d.t_c32 = p.t_c32;
+    d.diag_tab64 = p.diag_tab64;
+    d.diag_tab32 = p.diag_tab32;
+    d.diag_rest = p.diag_rest;
+    d.n_diag_rest = p.n_diag_rest;
     return d;
 }
 

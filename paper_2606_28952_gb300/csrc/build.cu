@@ -440,12 +440,35 @@ void jw_fermion_raw_device(int n, int nterms, const int *nf, const int *modes, c
     PS_CUDA(cudaStreamSynchronize(st));
 }
 
+// T(t_lo) over the x = 0 group's terms with z_hi = 0 (the first term of a
+// segment, terms being sorted by z_hi inside it), FP64 sums in segment order
+__global__ void k_diag_table(int n_lo, int nseg, const int32_t *s_t0, const uint32_t *s_zlo,
+                             const uint32_t *t_zhi, const double2 *t_c64, double2 *tab64, float2 *tab32) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = 1u << n_lo;
+    if (t >= n) return;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < nseg; ++s) {
+        const int t0 = s_t0[s];
+        if (t_zhi[t0] != 0u) continue;
+        const double2 c = t_c64[t0];
+        const bool neg = __popc(s_zlo[s] & t) & 1;
+        re += neg ? -c.x : c.x;
+        im += neg ? -c.y : c.y;
+    }
+    tab64[t] = make_double2(re, im);
+    const float hr = (float)re, hi = (float)im;
+    tab32[t] = make_float2(hr, hi);
+    tab32[n + t] = make_float2((float)(re - (double)hr), (float)(im - (double)hi));
+}
+
 void free_plan(const Allocator &al, Plan &p) {
     dev_free(al, p.pc_xhi); dev_free(al, p.pc_i0); dev_free(al, p.it_xlo); dev_free(al, p.it_s0);
     dev_free(al, p.it_xhi);
     dev_free(al, p.s_xhi);
     dev_free(al, p.s_zlo); dev_free(al, p.s_t0);
     dev_free(al, p.t_zhi); dev_free(al, p.t_c64); dev_free(al, p.t_c32);
+    dev_free(al, p.diag_tab64); dev_free(al, p.diag_tab32); dev_free(al, p.diag_rest);
     dev_free(al, p.partials);
     dev_free(al, p.split_buf);
     p = Plan();
@@ -581,6 +604,29 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
         p.s_xhi = static_cast<uint32_t *>(upload(s_xhi.data(), (S > 0 ? S : 0) * sizeof(uint32_t)));
     }
     p.it_s0 = static_cast<int32_t *>(upload(it_s0.data(), it_s0.size() * sizeof(int32_t)));
+    if (p.nseg_diag > 0 && n_lo <= kDiagTabBits) {
+        // diagonal table, and the diagonal segments left with a z_hi != 0 term
+        const int nd = p.nseg_diag;
+        std::vector<int32_t> st0(nd + 1);
+        PS_CUDA(cudaMemcpy(st0.data(), p.s_t0, (nd + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        const int32_t nt = st0[nd] - st0[0];
+        std::vector<uint32_t> tzhi(nt > 0 ? nt : 1);
+        if (nt > 0) PS_CUDA(cudaMemcpy(tzhi.data(), p.t_zhi + st0[0], nt * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        std::vector<int32_t> rest;
+        for (int sg = 0; sg < nd; ++sg) {
+            const int32_t a = st0[sg] - st0[0], b = st0[sg + 1] - st0[0];
+            if (b - a >= 2 || (b - a == 1 && tzhi[a] != 0u)) rest.push_back(sg);
+        }
+        const int64_t ntab = 1ll << n_lo;
+        p.diag_tab64 = static_cast<double2 *>(dev_alloc(al, ntab * sizeof(double2)));
+        p.diag_tab32 = static_cast<float2 *>(dev_alloc(al, 2 * ntab * sizeof(float2)));
+        k_diag_table<<<nblk(ntab), 256, 0, st>>>(n_lo, nd, p.s_t0, p.s_zlo, p.t_zhi, p.t_c64, p.diag_tab64,
+                                                  p.diag_tab32);
+        PS_CUDA(cudaGetLastError());
+        p.n_diag_rest = (int32_t)rest.size();
+        p.diag_rest = static_cast<int32_t *>(upload(rest.data(), rest.size() * sizeof(int32_t)));
+        PS_CUDA(cudaStreamSynchronize(st));
+    }
     h->plans[h->nplans] = p;
     return h->plans[h->nplans++];
 }

@@ -138,6 +138,13 @@ struct Plan {
     uint32_t *t_zhi = nullptr;         // [M] (segment order)
     double2 *t_c64 = nullptr;          // [M] FP64 coefficients
     float2 *t_c32 = nullptr;           // [M] FP32 coefficients
+    // x = 0 group, n_lo <= kDiagTabBits: the part of its terms with z_hi = 0
+    // tabulated over the low bits, T(t_lo) = sum c_k (-1)^popc(z_lo,k & t_lo)
+    // (FP64, and FP32 hi + lo), and the segments that keep a term with z_hi != 0
+    double2 *diag_tab64 = nullptr;     // [2^n_lo]
+    float2 *diag_tab32 = nullptr;      // [2 * 2^n_lo]: hi parts, then lo parts
+    int32_t *diag_rest = nullptr;      // [n_diag_rest] segment indices
+    int32_t n_diag_rest = 0;
     std::vector<int64_t> h_pc_cumw;   // [P+1] cumulative per-piece work estimate
     std::vector<TunedEntry> tuned;     // autotuned launch shapes per (sector, dtype)
     // reduction scratch for pauli_expect
@@ -147,6 +154,8 @@ struct Plan {
     void *split_buf = nullptr;
     int64_t split_cap = 0;
 };
+
+constexpr int kDiagTabBits = 12;
 
 struct PlanLimits {
     static constexpr int kItemsPerPiece = 64;

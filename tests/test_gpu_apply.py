@@ -77,6 +77,55 @@ def test_apply_full_space_complex_sum(ps, dt, n, n_lo):
     assert _rel(out, ref) <= TOL[dt]
 
 
+def _diag_rich_terms(n, seed):
+    """Complex sum with a large x = 0 group (Z strings on low-only, high-only and
+    crossing bit sets, the identity) and a few off-diagonal groups."""
+    rng = np.random.default_rng(seed)
+    xs, zs, cre, cim = [0], [0], [0.7], [0.0]
+    for _ in range(120):
+        xs.append(0)
+        zs.append(int(rng.integers(1, 1 << n)))
+        cre.append(rng.normal())
+        cim.append(0.3 * rng.normal())
+    for _ in range(20):
+        xm = int(rng.integers(1, 1 << n))
+        for _ in range(3):
+            xs.append(xm)
+            zs.append(int(rng.integers(0, 1 << n)))
+            cre.append(rng.normal())
+            cim.append(rng.normal())
+    return (np.array(xs, np.uint64), np.array(zs, np.uint64), np.array(cre), np.array(cim))
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("n_lo", [5, 10, 12, 13])
+def test_apply_direct_diagonal_table(ps, dt, n_lo):
+    """The small-operator (direct) gather with the x = 0 group's z_hi = 0 part
+    tabulated over the low bits (n_lo <= 12) and without (13), against the
+    oracle and against the staged gather."""
+    n = 15
+    x_, z_, cre, cim = _diag_rich_terms(n, 40 + n_lo)
+    H = ps.PauliSum.from_terms(n, x_, z_, cre, cim, form=ps.XZ)
+    R = oracle.build_sum(n, x_, z_, None, cre, cim, letter_form=False)
+    S = ps.Sector.full(n, n_lo)
+    So = oracle.Sector.full(n)
+    psi = w.random_state(1 << n, 17)
+    x = _to_dev(psi, dt)
+    ref = oracle.apply(So, R, x.cpu().numpy().astype(np.complex128))
+    outs = []
+    for direct in (1, 0):
+        ps.prepare(H, S)
+        c = ps.LaunchConfig(cols_per_thread=4 if direct else 1, staged_rows=1, row_split=1, direct=direct, ranked=0,
+                            ms=0.0)
+        ps.set_launch_config(H, S, _tdt(dt), c)
+        out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+        assert _rel(out, ref) <= TOL[dt], direct
+        outs.append(out)
+        r = ps.expect(H, S, x).cpu().numpy()
+        e_ref = np.vdot(x.cpu().numpy().astype(np.complex128), ref)
+        assert abs(complex(r[0], r[1]) - e_ref) <= TOL[dt] * np.linalg.norm(ref) * np.linalg.norm(psi)
+
+
 @pytest.mark.parametrize("dt", ["c128", "c64"])
 def test_apply_multiblock_sz0_xxz(ps, dt):
     """Open XXZ chain, 14 sites, Sz = 0 as 8 product blocks (k, 7-k) of a 7|7 split."""
