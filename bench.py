@@ -315,6 +315,40 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_other = ev0.elapsed_time(ev1) / 1e3 / 5
 
+    # kernels per pauli_apply: the gather, plus the fixed-order sum of the row-piece split
+    lc = ps.launch_config(H, S, tdt)
+    launches_per_apply = 2 if lc["row_split"] > 1 and not lc["direct"] else 1
+
+    # side measurement: one pair-double rotation on the 32-qubit (8a,8b) sector
+    # (165,636,900 amplitudes, 1.3 GB complex64) against the HBM roof of the
+    # amplitudes it touches (read + write of every pair with f != 0)
+    rot = None
+    if not args.no_rotate:
+        norb = w.PES_NORB
+        Sr = ps.Sector.molecular(norb, norb // 2, norb // 2)
+        Gr = ps.PauliSum.jw_fermion(2 * norb, w.pair_double_generator(norb, 0, norb - 1))
+        phi = torch.zeros(Sr.dim, dtype=torch.complex64, device=dev)
+        phi.fill_(1.0 / math.sqrt(Sr.dim))
+        ps.rotate(Gr, Sr, 0.1, phi)
+        torch.cuda.synchronize()
+        nrot = 20
+        ev0.record(stream)
+        for _ in range(nrot):
+            ps.rotate(Gr, Sr, 0.1, phi)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_rot = ev0.elapsed_time(ev1) / 1e3 / nrot
+        # pairs with f != 0: orbital 0 doubly occupied and orbital norb-1 empty, or the
+        # reverse; the other norb-2 orbitals hold (k-1) alpha and (k-1) beta electrons
+        k = norb // 2
+        touched = 2 * math.comb(norb - 2, k - 1) ** 2
+        rot_bytes = 2 * 8 * touched
+        rot = {"ms": t_rot * 1e3, "sector_dim": Sr.dim, "touched_amplitudes": touched,
+               "compulsory_bytes": rot_bytes, "achieved_gbs": rot_bytes / t_rot / 1e9,
+               "hbm_frac": rot_bytes / t_rot / 1e9 / hbm_peak}
+        del phi
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, nrows, dt, est = oracle_rate(seconds=args.ref_seconds)
@@ -334,17 +368,20 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "alu", "achieved": achieved_gups, "peak": popc_peak, "unit": "Gupd/s",
                          "frac": achieved_gups / popc_peak,
                          "traffic": profiled_traffic("k_apply_mol24_c64.json") if args.dtype == "c64" else None,
-                         "note": (f"updates U={U} per launch / CUDA-event step time; peak = {sms} SMs x "
+                         "note": (f"updates U={U} per launch / CUDA-event step time (the step is the gather "
+                                  f"kernel plus, when rows are split, its fixed-order combine: "
+                                  f"{launches_per_apply} launch(es) per step); peak = {sms} SMs x "
                                   f"{POPC_PER_CLK_SM} popcounts/clk x {sm_mhz_max:.0f} MHz (one parity per "
                                   f"update); HBM view: {alg_bytes} compulsory bytes -> {achieved_gbs:.2f} GB/s "
                                   f"= {achieved_gbs / hbm_peak:.5f} of {peak_kind} {hbm_peak} GB/s")},
             "cpu_baseline": cpu,
             "e2e": {"value": world * U / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * launches_per_apply,
             "clocks": clk,
             "side": {"expect_ms": t_expect * 1e3, f"apply_{'c128' if tdt == torch.complex64 else 'c64'}_ms": t_other * 1e3,
-                     "step_times_ms_min_max": [min(times_ms), max(times_ms)]},
+                     "step_times_ms_min_max": [min(times_ms), max(times_ms)],
+                     "launch_shape": lc, "rotate_pair_double_32q_c64": rot},
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -360,16 +397,16 @@ def run_xxz(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    n = w.XXZ_SITES
+    n = args.sites or w.XXZ_SITES
     x, z, cre, cim = w.xxz_terms(n, w.XXZ_SEED)
     H = ps.PauliSum.from_terms(n, x, z, cre, cim)
     if args.workload == "xxz30":
         S = ps.Sector.full(n, args.n_lo or 10)
-        label = f"xxz30 full space 2^30, split {S.n_lo if S.n_lo else 10}|{n - (args.n_lo or 10)}"
+        label = f"xxz{n} full space 2^{n}, split {S.n_lo if S.n_lo else 10}|{n - (args.n_lo or 10)}"
     else:
         nl = args.n_lo or 12
         S = ps.Sector(n, ps.BLOCKS, nl, [(k, n // 2 - k) for k in range(0, min(nl, n // 2) + 1)])
-        label = f"xxz30 Sz=0 blocks, split {nl}|{n - nl}, D={S.dim}"
+        label = f"xxz{n} Sz=0 blocks, split {nl}|{n - nl}, D={S.dim}"
     ps.prepare(H, S)
     xc, _, _ = H.export()
     # term updates of one apply in the full space = M * 2^n; in a sector count per term
@@ -401,6 +438,7 @@ def run_xxz(args, rank, world, local_rank):
     psi.zero_()
     neel = torch.tensor([w.neel_config(n)], dtype=torch.int64, device=dev)
     psi[S.rank(neel)[0].item()] = 1.0
+    e_start = ps.expect(H, S, psi)[0].item()
     k = ps.Krylov(H, S, m=20, dtype=torch.complex64)
     k.step(psi, 0.05, nsteps=1, graph=True)  # capture
     torch.cuda.synchronize()
@@ -413,6 +451,7 @@ def run_xxz(args, rank, world, local_rank):
     clk = clocks.stop()
     t_step = e0.elapsed_time(e1) / 1e3 / args.krylov_steps
     nrm = torch.linalg.vector_norm(psi).item()
+    e_end = ps.expect(H, S, psi)[0].item()
     step_vectors = 9 * 20 + 4
     line = {
         "metric": "Krylov real-time steps/s (m=20, dt=0.05)", "value": 1.0 / t_step, "unit": "steps/s",
@@ -423,7 +462,8 @@ def run_xxz(args, rank, world, local_rank):
                   "hbm_frac": apply_bytes / t_apply / 1e9 / hbm_peak, "peak": f"{peak_kind} {hbm_peak} GB/s"},
         "step_bytes_compulsory": step_vectors * S.dim * 8,
         "step_hbm_frac": step_vectors * S.dim * 8 / t_step / 1e9 / hbm_peak,
-        "norm_after": nrm, "clocks": clk,
+        "norm_after": nrm, "energy_start": e_start, "energy_after": e_end,
+        "steps_total": 1 + args.krylov_steps, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -501,6 +541,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["mol24", "xxz30", "xxz30-sz0", "batched64"], default="mol24")
     ap.add_argument("--n-lo", type=int, default=0)
+    ap.add_argument("--sites", type=int, default=0, help="XXZ chain length (default 30; smaller for profiling)")
     ap.add_argument("--krylov-steps", type=int, default=5)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -509,6 +550,7 @@ def main():
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rotate", action="store_true", help="skip the 32-qubit rotation side measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -93,3 +93,41 @@ def test_krylov_molecular_random_state(ps):
     out, _ = _run(ps, H, S, psi0, 0.02, 5, torch.complex128, True, m=16)
     Hs = dense.sector_matrix(2 * norb, R.x, R.z, R.c, So.configs())
     assert np.linalg.norm(out - dense.propagate(Hs, psi0, 0.1)) <= 1e-10
+
+
+def test_krylov_30_sites_full_space_agrees_with_sz0(ps):
+    """The 30-site chain at full size: the Neel state lies in Sz = 0 and H keeps Sz,
+    so 3 graph-replayed steps in the full 2^30 space (complex64, 21 Krylov vectors
+    of 8.6 GB) and in the Sz = 0 block sector (D = 155,117,520) must give the same
+    amplitudes on Sz = 0 and nothing outside it; norm and energy are conserved.
+    (The exact propagator is out of reach at this size; this is the pin.)"""
+    import torch
+    n = w.XXZ_SITES
+    x, z, cre, cim = w.xxz_terms(n, w.XXZ_SEED)
+    H = ps.PauliSum.from_terms(n, x, z, cre, cim)
+    Sf = ps.Sector.full(n, 10)
+    nl = 12
+    Sz = ps.Sector(n, ps.BLOCKS, nl, [(k, n // 2 - k) for k in range(0, min(nl, n // 2) + 1)])
+    neel = w.neel_config(n)
+    dt, nsteps = 0.05, 3
+    res = {}
+    for name, S in (("sz0", Sz), ("full", Sf)):
+        psi = torch.zeros(S.dim, dtype=torch.complex64, device="cuda")
+        psi[S.rank(torch.tensor([neel], dtype=torch.int64, device="cuda"))[0].item()] = 1.0
+        e0 = ps.expect(H, S, psi)[0].item()
+        k = ps.Krylov(H, S, m=20, dtype=torch.complex64)
+        k.step(psi, dt, nsteps=nsteps, graph=True)
+        r = ps.expect(H, S, psi).cpu().numpy()
+        assert abs(r[3] - 1.0) < 1e-5          # norm
+        assert abs(r[0] - e0) < 1e-4 * max(1.0, abs(e0))  # energy
+        res[name] = psi
+        del k
+        torch.cuda.empty_cache()
+    # Sz = 0 amplitudes of the full-space result, in the block sector's order
+    cfg = Sz.unrank(torch.arange(Sz.dim, dtype=torch.int64, device="cuda"))
+    full_on_sz0 = res["full"][cfg]
+    a, b = full_on_sz0, res["sz0"]
+    assert (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item() < 2e-5
+    # and the full-space vector carries no weight outside Sz = 0
+    outside = 1.0 - torch.linalg.vector_norm(full_on_sz0).item() ** 2
+    assert abs(outside) < 1e-5
