@@ -226,7 +226,11 @@ int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const void *psi, i
  * one X mask, PAULI_ENOTHERMITIAN if a letter-form coefficient has an
  * imaginary part above 1e-12 max|C|.  If some t in the sector has
  * t XOR x outside it with f_t != 0, the device status word of G gets
- * PAULI_ESECTOR (see pauli_status) and those amplitudes are left unchanged. */
+ * PAULI_ESECTOR (see pauli_status) and those amplitudes are left unchanged.
+ * On a single-product-block sector the first rotation by G checks that once
+ * (synchronising st; make that first call outside stream capture) and, if G
+ * keeps the sector, builds a list of the pairs {t, t XOR x} inside it; later
+ * rotations visit only those pairs.  pauli_rotate_adjoint shares the list. */
 int pauli_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, int dtype,
                  pauli_stream_t st);
 

@@ -3,6 +3,7 @@
 // Each entry point validates its arguments on the host, converts failures into
 // status codes (no exception crosses the ABI) and enqueues the kernels of
 // build.cu, sector.cu and apply.cu.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -124,6 +125,8 @@ pauli_sum *new_sum(int n) {
 void destroy_sum(pauli_sum *h) {
     if (!h) return;
     for (int i = 0; i < h->nplans; ++i) free_plan(h->al, h->plans[i]);
+    for (int i = 0; i < h->nrot; ++i) dev_free(h->al, h->rot[i].tab);
+    dev_free(h->al, h->leak_flag);
     dev_free(h->al, h->x);
     dev_free(h->al, h->z);
     dev_free(h->al, h->c);
@@ -389,6 +392,8 @@ int pauli_sector_create(int n_qubits, int kind, int n_lo, int n_blocks, const in
         }
         pauli_sector *s = new pauli_sector();
         s->magic = kSectorMagic;
+        static std::atomic<uint64_t> next_uid{1};
+        s->uid = next_uid.fetch_add(1);
         s->al = current_allocator();
         try {
             init_sector_view(s->v, n_qubits, kind, n_lo, n_blocks, k_lo, k_hi);
@@ -508,7 +513,7 @@ int pauli_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, i
         if (G->m == 0) return;
         PS_CHECK(G->G == 1, PAULI_EINVAL, "rotation generator must have exactly one X mask");
         PS_CHECK(G->hermitian, PAULI_ENOTHERMITIAN, "rotation generator is not Hermitian");
-        launch_rotate(G, s->v, theta, psi, dtype, (cudaStream_t)st);
+        launch_rotate(G, s, theta, psi, dtype, (cudaStream_t)st);
     });
 }
 
@@ -530,7 +535,7 @@ int pauli_rotate_adjoint(pauli_sum *G, const pauli_sector *s, double theta, void
             PS_CUDA(cudaMemsetAsync(result, 0, 2 * sizeof(double), (cudaStream_t)st));
             return;
         }
-        launch_rotate_adjoint(G, s->v, theta, phi, lam, dtype, result, (cudaStream_t)st);
+        launch_rotate_adjoint(G, s, theta, phi, lam, dtype, result, (cudaStream_t)st);
     });
 }
 

@@ -35,10 +35,12 @@ template <typename R> __device__ __forceinline__ void sincos_r(R a, R *s, R *c);
 template <> __device__ __forceinline__ void sincos_r<float>(float a, float *s, float *c) { sincosf(a, s, c); }
 template <> __device__ __forceinline__ void sincos_r<double>(double a, double *s, double *c) { sincos(a, s, c); }
 
+// check_only: record a sector leak in *status and change nothing (the one-time
+// leak check that admits a generator to k_rotate_pairs)
 template <typename R, bool FULL>
 __global__ void __launch_bounds__(kThreads)
 k_rotate(SectorView v, Geom geo, int64_t m, uint64_t x, const uint64_t *__restrict__ z,
-         const double2 *__restrict__ c, R theta, typename Cx<R>::T *psi, int *status) {
+         const double2 *__restrict__ c, R theta, typename Cx<R>::T *psi, int *status, int check_only) {
     using C2 = typename Cx<R>::T;
     __shared__ uint64_t sm_z[kRotChunk];
     __shared__ C2 sm_c[kRotChunk];
@@ -84,6 +86,7 @@ k_rotate(SectorView v, Geom geo, int64_t m, uint64_t x, const uint64_t *__restri
         }
         sidx = v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb] + (int64_t)__ldg(v.rank_lo + slo);
     }
+    if (check_only) return;
     const int64_t tidx = rc.own_base + col;
     if (x == 0) {
         // diagonal generator: psi_t <- exp(-i theta f_t) psi_t (f_t real)
@@ -244,6 +247,97 @@ k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const
     }
 }
 
+// The same rotation (ADJ: the adjoint step of k_rotate_adj) over the listed
+// pairs only (RotPairs): no work for targets whose partner leaves the block, and
+// each pair is visited once.  Fixed grid, block-strided over pair ids.
+template <typename R, bool ADJ>
+__global__ void __launch_bounds__(kThreads)
+k_rotate_pairs(int64_t npairs, int64_t nlo, const uint32_t *__restrict__ tab, int64_t nhi, int n_lo, int64_t off,
+               int64_t dlo, int64_t m, uint64_t x, const uint64_t *__restrict__ z, const double2 *__restrict__ c,
+               R theta, typename Cx<R>::T *phi, typename Cx<R>::T *lam, double *partials) {
+    using C2 = typename Cx<R>::T;
+    __shared__ uint64_t sm_z[kRotPairTerms];
+    __shared__ C2 sm_c[kRotPairTerms];
+    __shared__ double red[2][kThreads / 32];
+    const int tid = threadIdx.x;
+    for (int k = tid; k < m; k += kThreads) {
+        sm_z[k] = z[k];
+        const double2 cc = c[k];
+        C2 cv;
+        cv.x = (R)cc.x;
+        cv.y = (R)cc.y;
+        sm_c[k] = cv;
+    }
+    __syncthreads();
+    const uint32_t *pat_lo = tab, *rt_lo = tab + nlo, *rs_lo = tab + 2 * nlo;
+    const uint32_t *pat_hi = tab + 3 * nlo, *rt_hi = pat_hi + nhi, *rs_hi = pat_hi + 2 * nhi;
+    DotAcc<R> dot;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + tid; i < npairs; i += (int64_t)gridDim.x * kThreads) {
+        const int64_t h = i / nlo, l = i - h * nlo;
+        const uint64_t t = ((uint64_t)__ldg(pat_hi + h) << n_lo) | (uint64_t)__ldg(pat_lo + l);
+        const uint64_t s = t ^ x;
+        R fr = R(0), fi = R(0);
+        for (int k = 0; k < m; ++k) {
+            const uint32_t par = __popcll(sm_z[k] & s);
+            fr += flip(sm_c[k].x, par);
+            fi += flip(sm_c[k].y, par);
+        }
+        const R mag = sqrt(fr * fr + fi * fi);
+        if (mag == R(0)) continue;
+        const int64_t it = off + (int64_t)__ldg(rt_hi + h) * dlo + __ldg(rt_lo + l);
+        const int64_t is = off + (int64_t)__ldg(rs_hi + h) * dlo + __ldg(rs_lo + l);
+        R sn, cs;
+        sincos_r<R>(theta * mag, &sn, &cs);
+        const R q = sn / mag;
+        auto rot = [&](const C2 &u, const C2 &w, C2 &nu, C2 &nw) {
+            const R wr = fr * w.x - fi * w.y, wi = fr * w.y + fi * w.x;
+            const R ur = fr * u.x + fi * u.y, ui = fr * u.y - fi * u.x;
+            nu.x = cs * u.x + q * wi;
+            nu.y = cs * u.y - q * wr;
+            nw.x = cs * w.x + q * ui;
+            nw.y = cs * w.y - q * ur;
+        };
+        const C2 a = phi[it], b = phi[is];
+        C2 na, nb;
+        rot(a, b, na, nb);
+        phi[it] = na;
+        phi[is] = nb;
+        if (ADJ) {
+            const C2 la = lam[it], lb = lam[is];
+            // conj(la) f b + conj(lb) conj(f) a, from the input values
+            C2 fb, fa;
+            fb.x = fr * b.x - fi * b.y;
+            fb.y = fr * b.y + fi * b.x;
+            fa.x = fr * a.x + fi * a.y;
+            fa.y = fr * a.y - fi * a.x;
+            dot.add(la, fb);
+            dot.add(lb, fa);
+            C2 nla, nlb;
+            rot(la, lb, nla, nlb);
+            lam[it] = nla;
+            lam[is] = nlb;
+        }
+    }
+    if (ADJ) {
+        double mr = dot.get_re(), mi = dot.get_im();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mr += __shfl_down_sync(0xffffffffu, mr, o);
+            mi += __shfl_down_sync(0xffffffffu, mi, o);
+        }
+        if ((tid & 31) == 0) {
+            red[0][tid >> 5] = mr;
+            red[1][tid >> 5] = mi;
+        }
+        __syncthreads();
+        if (tid < 2) {
+            double acc = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) acc += red[tid][w];
+            partials[(int64_t)blockIdx.x * 4 + tid] = acc;
+        }
+    }
+}
+
 }  // namespace
 
 // 227 KB of shared memory per block on sm_103a, less room for the kernel's static arrays
@@ -382,9 +476,141 @@ static uint64_t group_mask0(pauli_sum *G) {
     return G->gx0_host;
 }
 
-void launch_rotate_adjoint(pauli_sum *G, const SectorView &v, double theta, void *phi, void *lam, int dtype,
+// colex rank of a string among the strings of the same popcount: sum over its
+// set bits p_0 < p_1 < ... of C(p_j, j + 1)
+static uint32_t colex_rank(uint32_t b) {
+    uint64_t r = 0;
+    int j = 0;
+    while (b) {
+        const int p = __builtin_ctz(b);
+        uint64_t cnk = 0;
+        if (p >= j + 1) {
+            cnk = 1;
+            for (int i = 0; i < j + 1; ++i) cnk = cnk * (uint64_t)(p - i) / (uint64_t)(i + 1);
+        }
+        r += cnk;
+        ++j;
+        b &= b - 1;
+    }
+    return (uint32_t)r;
+}
+
+// The strings of `bits` bits with popcount k that have exactly half of xm's bits
+// set (and bit `need`, if need >= 0), ascending, with their ranks and the ranks
+// of b ^ xm.
+static void half_pairs(int bits, int k, uint32_t xm, int need, std::vector<uint32_t> &pat,
+                       std::vector<uint32_t> &rt, std::vector<uint32_t> &rs) {
+    const int a = __builtin_popcount(xm);
+    if (k < 0 || k > bits) return;
+    if (k == 0) {
+        if (a == 0 && need < 0) {
+            pat.push_back(0);
+            rt.push_back(0);
+            rs.push_back(0);
+        }
+        return;
+    }
+    // Gosper's rule: the k-subsets of `bits` bits in increasing order (= colex rank order)
+    uint64_t b = (1ull << k) - 1ull;
+    const uint64_t lim = 1ull << bits;
+    uint32_t rank = 0;
+    while (b < lim) {
+        const uint32_t bb = (uint32_t)b;
+        if (2 * __builtin_popcount(bb & xm) == a && (need < 0 || ((bb >> need) & 1u))) {
+            pat.push_back(bb);
+            rt.push_back(rank);
+            rs.push_back(colex_rank(bb ^ xm));
+        }
+        ++rank;
+        const uint64_t cbit = b & (~b + 1ull), r = b + cbit;
+        b = (((r ^ b) >> 2) / cbit) | r;
+    }
+}
+
+// One-time check: does G move amplitude out of the sector?  (k_rotate in
+// check-only mode; the answer is read back, so the call synchronises st once.)
+static bool rotation_leaks(pauli_sum *G, const SectorView &v, uint64_t x, cudaStream_t st) {
+    if (!G->leak_flag) G->leak_flag = static_cast<int *>(dev_alloc(G->al, sizeof(int)));
+    PS_CUDA(cudaMemsetAsync(G->leak_flag, 0, sizeof(int), st));
+    const Geom geo = make_geom(v, kThreads);
+    const int64_t nct = geo.cta_off[v.nblk];
+    if (nct > 0) {
+        PS_CHECK(nct < (1ll << 31), PAULI_EUNSUPPORTED, "rotate: too many thread blocks");
+        k_rotate<double, false><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, 0.0, nullptr,
+                                                                    G->leak_flag, 1);
+        PS_LAUNCH_CHECK();
+    }
+    int flag = 0;
+    PS_CUDA(cudaMemcpyAsync(&flag, G->leak_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    return flag != 0;
+}
+
+// Pair tables of (G, sector) for k_rotate_pairs, built on first use and kept in G
+// (the last kRotPairsCache sectors); nullptr where the per-target kernel applies:
+// full space, several blocks, x = 0, more than kRotPairTerms terms, or a generator
+// that leaks out of the sector (its leaks are then recorded on every call).
+static const RotPairs *rotation_pairs(pauli_sum *G, const pauli_sector *sec, uint64_t x, cudaStream_t st) {
+    const SectorView &v = sec->v;
+    if (v.kind != PAULI_SECTOR_BLOCKS || v.nblk != 1 || x == 0 || G->m > kRotPairTerms) return nullptr;
+    for (int i = 0; i < G->nrot; ++i)
+        if (G->rot[i].sector_uid == sec->uid) return G->rot[i].leaks ? nullptr : &G->rot[i];
+    RotPairs rp;
+    rp.sector_uid = sec->uid;
+    rp.leaks = rotation_leaks(G, v, x, st) ? 1 : 0;
+    if (!rp.leaks) {
+        const uint32_t lomask = (uint32_t)((1ull << v.n_lo) - 1ull);
+        const uint32_t xlo = (uint32_t)(x & lomask), xhi = (uint32_t)(x >> v.n_lo);
+        const int b0 = __builtin_ctzll(x);
+        std::vector<uint32_t> plo, rtlo, rslo, phi, rthi, rshi;
+        half_pairs(v.n_lo, v.klo[0], xlo, b0 < v.n_lo ? b0 : -1, plo, rtlo, rslo);
+        half_pairs(v.n_hi, v.khi[0], xhi, b0 >= v.n_lo ? b0 - v.n_lo : -1, phi, rthi, rshi);
+        rp.nlo = (int64_t)plo.size();
+        rp.nhi = (int64_t)phi.size();
+        std::vector<uint32_t> tab;
+        tab.reserve(3 * (rp.nlo + rp.nhi));
+        for (auto *vv : {&plo, &rtlo, &rslo, &phi, &rthi, &rshi}) tab.insert(tab.end(), vv->begin(), vv->end());
+        if (!tab.empty()) {
+            rp.tab = static_cast<uint32_t *>(dev_alloc(G->al, tab.size() * sizeof(uint32_t)));
+            PS_CUDA(cudaMemcpyAsync(rp.tab, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+            PS_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+    if (G->nrot == kRotPairsCache) {
+        dev_free(G->al, G->rot[0].tab);
+        for (int i = 1; i < kRotPairsCache; ++i) G->rot[i - 1] = G->rot[i];
+        --G->nrot;
+    }
+    G->rot[G->nrot++] = rp;
+    const RotPairs &r = G->rot[G->nrot - 1];
+    return r.leaks ? nullptr : &r;
+}
+
+template <typename R, bool ADJ>
+static void launch_pairs(const RotPairs &rp, pauli_sum *G, const SectorView &v, uint64_t x, double theta, void *phi,
+                         void *lam, double *partials, unsigned grid, cudaStream_t st) {
+    using C2 = typename Cx<R>::T;
+    k_rotate_pairs<R, ADJ><<<grid, kThreads, 0, st>>>(rp.nlo * rp.nhi, rp.nlo > 0 ? rp.nlo : 1, rp.tab, rp.nhi,
+                                                     v.n_lo, v.off[0], v.dlo[0], G->m, x, G->z, G->c, (R)theta,
+                                                     static_cast<C2 *>(phi), static_cast<C2 *>(lam), partials);
+    PS_LAUNCH_CHECK();
+}
+
+void launch_rotate_adjoint(pauli_sum *G, const pauli_sector *sec, double theta, void *phi, void *lam, int dtype,
                            double *result, cudaStream_t st) {
+    const SectorView &v = sec->v;
     const uint64_t x = group_mask0(G);
+    if (const RotPairs *rp = rotation_pairs(G, sec, x, st)) {
+        DotScratch &d = dot_scratch();
+        const int64_t np = rp->nlo * rp->nhi;
+        const int64_t need = (np + kThreads - 1) / kThreads;
+        const unsigned grid = (unsigned)(need < d.blocks ? (need > 0 ? need : 1) : d.blocks);
+        if (dtype == PAULI_C64) launch_pairs<float, true>(*rp, G, v, x, theta, phi, lam, d.partials, grid, st);
+        else launch_pairs<double, true>(*rp, G, v, x, theta, phi, lam, d.partials, grid, st);
+        launch_reduce2(d.partials, grid, result, st);
+        return;
+    }
+
     const Geom geo = make_geom(v, kThreads);
     const int64_t nwork = geo.cta_off[v.nblk];
     DotScratch &d = dot_scratch();
@@ -405,20 +631,31 @@ void launch_rotate_adjoint(pauli_sum *G, const SectorView &v, double theta, void
     launch_reduce2(d.partials, grid, result, st);
 }
 
-void launch_rotate(pauli_sum *G, const SectorView &v, double theta, void *psi, int dtype,
+void launch_rotate(pauli_sum *G, const pauli_sector *sec, double theta, void *psi, int dtype,
                    cudaStream_t st) {
+    const SectorView &v = sec->v;
     const uint64_t x = group_mask0(G);
+    if (const RotPairs *rp = rotation_pairs(G, sec, x, st)) {
+        const int64_t np = rp->nlo * rp->nhi;
+        if (np == 0) return;
+        const int blocks = num_sms() * 8;
+        const int64_t need = (np + kThreads - 1) / kThreads;
+        const unsigned grid = (unsigned)(need < blocks ? need : blocks);
+        if (dtype == PAULI_C64) launch_pairs<float, false>(*rp, G, v, x, theta, psi, nullptr, nullptr, grid, st);
+        else launch_pairs<double, false>(*rp, G, v, x, theta, psi, nullptr, nullptr, grid, st);
+        return;
+    }
     const Geom geo = make_geom(v, kThreads);
     const int64_t nct = geo.cta_off[v.nblk];
     if (nct == 0) return;
     PS_CHECK(nct < (1ll << 31), PAULI_EUNSUPPORTED, "rotate: too many thread blocks");
     const bool full = v.kind == PAULI_SECTOR_FULL;
     if (dtype == PAULI_C64) {
-        if (full) k_rotate<float, true><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, (float)theta, static_cast<float2 *>(psi), G->status);
-        else k_rotate<float, false><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, (float)theta, static_cast<float2 *>(psi), G->status);
+        if (full) k_rotate<float, true><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, (float)theta, static_cast<float2 *>(psi), G->status, 0);
+        else k_rotate<float, false><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, (float)theta, static_cast<float2 *>(psi), G->status, 0);
     } else {
-        if (full) k_rotate<double, true><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, theta, static_cast<double2 *>(psi), G->status);
-        else k_rotate<double, false><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, theta, static_cast<double2 *>(psi), G->status);
+        if (full) k_rotate<double, true><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, theta, static_cast<double2 *>(psi), G->status, 0);
+        else k_rotate<double, false><<<(unsigned)nct, kThreads, 0, st>>>(v, geo, G->m, x, G->z, G->c, theta, static_cast<double2 *>(psi), G->status, 0);
     }
     PS_LAUNCH_CHECK();
 }

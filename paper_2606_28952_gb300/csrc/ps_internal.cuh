@@ -157,6 +157,19 @@ struct Plan {
 
 constexpr int kDiagTabBits = 12;
 
+// Pairs {t, t ^ x} of a single-group rotation on a single-block sector with both
+// members in the block, each listed once (the member with the lowest bit of x
+// set): pair i = h * nlo + l has t = (pat_hi[h] << n_lo) | pat_lo[l], index of t
+// off + rt_hi[h] * D_lo + rt_lo[l] and index of t ^ x off + rs_hi[h] * D_lo + rs_lo[l].
+struct RotPairs {
+    uint64_t sector_uid = 0;
+    int leaks = -1;            // the generator moves amplitude out of the sector: -1 unknown
+    int64_t nlo = 0, nhi = 0;  // table entries per half
+    uint32_t *tab = nullptr;   // pat_lo, rt_lo, rs_lo [nlo] each, then pat_hi, rt_hi, rs_hi [nhi]
+};
+constexpr int kRotPairsCache = 4;
+constexpr int kRotPairTerms = 512;  // generators with more terms keep the per-target kernel
+
 struct PlanLimits {
     static constexpr int kItemsPerPiece = 64;
     static constexpr int kSegsPerPiece = 512;
@@ -182,6 +195,9 @@ struct pauli_sum {
     int *status = nullptr;                // device status word
     uint64_t gx0_host = 0;                // gx[0] read back once (single-group rotations)
     bool gx0_known = false;
+    ps::RotPairs rot[ps::kRotPairsCache];   // pair tables per sector (single-group rotations)
+    int nrot = 0;
+    int *leak_flag = nullptr;             // device word of the one-time leak check
     ps::Plan plans[4];
     int nplans = 0;
 };
@@ -189,6 +205,7 @@ struct pauli_sum {
 struct pauli_sector {
     uint32_t magic;
     ps::Allocator al;
+    uint64_t uid = 0;  // unique per created sector (keys caches held by operators)
     ps::SectorView v;
     uint32_t *tables = nullptr;  // backing store of rank / list tables
 };
@@ -252,10 +269,9 @@ int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow
                        const LaunchChoice *force = nullptr);
 // elements of the split scratch a launch needs (0: no split)
 int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype, const LaunchChoice *force = nullptr);
-void launch_rotate(pauli_sum *G, const SectorView &v, double theta, void *psi, int dtype,
-                   cudaStream_t st);
+void launch_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, int dtype, cudaStream_t st);
 // <lam|G|phi> into result[0..1] (device), then phi, lam <- exp(-i theta G) phi, lam
-void launch_rotate_adjoint(pauli_sum *G, const SectorView &v, double theta, void *phi, void *lam, int dtype,
+void launch_rotate_adjoint(pauli_sum *G, const pauli_sector *s, double theta, void *phi, void *lam, int dtype,
                            double *result, cudaStream_t st);
 
 // linalg.cu: per-device scratch of FP64 partial sums shared by the reductions

@@ -81,6 +81,37 @@ def test_rotate_adjoint_matches_oracle(ps, dt, norb):
         assert np.linalg.norm(_host(lam) - oracle.rotate(So, Go, theta, lam0)) <= tol
 
 
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_pair_listed_rotation_single_excitations(ps, dt):
+    """Rotations whose X mask lies in the low half only (alpha excitations), the
+    high half only (beta) or both (pair doubles), on an open-shell single-block
+    sector: the pair-listed kernel against the oracle, forward and adjoint."""
+    import torch
+    norb, na, nb = 6, 3, 2
+    So = oracle.Sector.molecular(norb, na, nb)
+    S = ps.Sector.molecular(norb, na, nb)
+    tol = 1e-12 if dt == "c128" else 2e-6
+    gens = [w.single_generator(norb, p, q, spin) for (p, q, spin) in [(0, 4, 0), (1, 5, 1), (2, 3, 0), (0, 5, 1)]]
+    gens += [w.pair_double_generator(norb, 1, 4)]
+    for k, terms in enumerate(gens):
+        Go = oracle.fermion_sum(2 * norb, terms)
+        G = ps.PauliSum.jw_fermion(2 * norb, terms)
+        phi0 = w.random_state(S.dim, 70 + k)
+        lam0 = w.random_state(S.dim, 90 + k)
+        phi, lam = _dev(phi0, dt), _dev(lam0, dt)
+        ph_in, la_in = _host(phi), _host(lam)
+        th = 0.3 + 0.2 * k
+        ps.rotate(G, S, th, phi)
+        assert np.linalg.norm(_host(phi) - oracle.rotate(So, Go, th, ph_in)) <= tol, k
+        assert G.status() == 0
+        phi = _dev(phi0, dt)
+        out = torch.zeros(2, dtype=torch.float64, device="cuda")
+        ps.rotate_adjoint(G, S, -th, phi, lam, out)
+        mat = np.vdot(la_in, oracle.apply(So, Go, ph_in))
+        assert abs(complex(out[0].item(), out[1].item()) - mat) <= tol * max(1.0, abs(mat)), k
+        assert np.linalg.norm(_host(lam) - oracle.rotate(So, Go, -th, la_in)) <= tol, k
+
+
 def test_rotate_seq_is_the_sequence_of_rotations(ps):
     norb = 6
     S = ps.Sector.molecular(norb, 3, 3)
