@@ -434,6 +434,18 @@ def run_xxz(args, rank, world, local_rank):
     del out
     hbm_peak, peak_kind, _ = measured_peaks()
     apply_bytes = 2 * S.dim * 8 + H.m * 24 + H.n_groups * 16
+    if args.krylov_steps == 0:
+        # apply only (e.g. for a profiler capture of the gather at a reduced size)
+        if rank == 0:
+            print(json.dumps({
+                "metric": "H|psi> term-amplitude updates/s" if U else "H|psi> applies/s",
+                "value": (U / t_apply) if U else 1.0 / t_apply, "unit": "updates/s" if U else "applies/s",
+                "n_gpus": world, "steps": napp, "ms_per_step": t_apply * 1e3, "dtype": "c64/f32",
+                "data": "synthetic", "config": {"workload": label, "terms": H.m, "groups": H.n_groups},
+                "apply": {"ms": t_apply * 1e3, "compulsory_bytes": apply_bytes,
+                          "hbm_frac": apply_bytes / t_apply / 1e9 / hbm_peak,
+                          "peak": f"{peak_kind} {hbm_peak} GB/s"}}), flush=True)
+        return
     # --- Krylov steps from the Neel state ---
     psi.zero_()
     neel = torch.tensor([w.neel_config(n)], dtype=torch.int64, device=dev)
