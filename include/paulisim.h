@@ -315,7 +315,7 @@ int pauli_mlp_destroy(pauli_mlp *m);
  * with a rank table vs by bit pattern.  ms: measured time of one apply (0 if
  * not measured). */
 typedef struct {
-    int cols_per_thread;  /* 1, 2 or 4 */
+    int cols_per_thread;  /* 1, 2 or 4; 8 with rank-staged rows (else used as 4) */
     int staged_rows;      /* 1 or 2 */
     int row_split;        /* 1..16 */
     int direct;           /* 0 or 1 */

@@ -383,8 +383,13 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     const size_t extra = c.ranked ? rank_table_bytes(v.n_lo) : 0;
     // measured on the 24-qubit molecule (D_lo = 924): 4 columns per thread and a
     // single staged row (more resident CTAs) beat finer tiles and double buffering
-    int tpt = ch.tpt ? ch.tpt : env_int("PAULISIM_TPT", mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1));
-    if (tpt != 1 && tpt != 2 && tpt != 4) tpt = 1;
+    // rank-staged rows wider than ~100 KB leave one or two CTAs per SM: 8 columns per
+    // thread then give each thread more independent gathers to overlap
+    const bool wide_ranked = c.ranked && bb + extra > 100 * 1024 && mx >= 6 * kThreads;
+    int tpt = ch.tpt ? ch.tpt
+                     : env_int("PAULISIM_TPT", wide_ranked ? 8 : mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1));
+    if (tpt == 8 && !c.ranked) tpt = 4;
+    if (tpt != 1 && tpt != 2 && tpt != 4 && tpt != 8) tpt = 1;
     int nbuf = ch.nbuf ? ch.nbuf : env_int("PAULISIM_NBUF", 1);
     if (nbuf != 1 && nbuf != 2) nbuf = 1;
     if (nbuf * bb + extra > kMaxDynSmem) nbuf = 1;

@@ -600,6 +600,21 @@ k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__
                                           partials ? partials + (int64_t)blockIdx.x * 4 : nullptr, flags, smem);
 }
 
+// The same body for rank-staged rows: their shared-memory rows leave one or two
+// CTAs per SM, so the register budget is that of one resident CTA (without the
+// bound the compiler keeps to ~40 registers and spills; measured on the 32-qubit
+// sector: 7.27 s -> 5.01 s per apply together with 8 columns per thread).  The
+// other gathers keep the compiler's choice, which measured faster there than a
+// spill-free five- or four-CTA budget.
+template <typename R, int KIND, bool REALH, int TPT, int NBUF>
+__global__ void __launch_bounds__(kThreads, 1)
+k_apply_wide(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
+             typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
+    extern __shared__ __align__(16) char smem[];
+    apply_unit<R, KIND, REALH, TPT, NBUF>(v, geo, p, blockIdx.x, psi, out,
+                                          partials ? partials + (int64_t)blockIdx.x * 4 : nullptr, flags, smem);
+}
+
 // ---------------------------------------------------------------------------
 // Persistent batched launch: one grid of (#SM x resident) CTAs pulls work
 // units -- (state, row, column tile) -- from an atomic queue; states are
@@ -1062,15 +1077,18 @@ template <typename R, int KIND, bool REALH, int TPT, int NBUF>
 void launch_one(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, const PlanDev &pd, const void *in,
                 void *out, double *partials, int flags, cudaStream_t st) {
     using C2 = typename Cx<R>::T;
-    auto kern = k_apply<R, KIND, REALH, TPT, NBUF>;
-    static size_t attr_bytes = 48 * 1024;  // dynamic shared memory this kernel is opted in for
-    if (cfg.smem > attr_bytes) {
-        PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
-        attr_bytes = cfg.smem;
-    }
-    kern<<<(unsigned)cfg.nct, kThreads, cfg.smem, st>>>(v, geo, pd, static_cast<const C2 *>(in),
-                                                         static_cast<C2 *>(out), partials, flags);
-    PS_LAUNCH_CHECK();
+    auto run = [&](auto kern) {
+        static size_t attr_bytes = 48 * 1024;  // dynamic shared memory this kernel is opted in for
+        if (cfg.smem > attr_bytes) {
+            PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
+            attr_bytes = cfg.smem;
+        }
+        kern<<<(unsigned)cfg.nct, kThreads, cfg.smem, st>>>(v, geo, pd, static_cast<const C2 *>(in),
+                                                             static_cast<C2 *>(out), partials, flags);
+        PS_LAUNCH_CHECK();
+    };
+    if constexpr (KIND == KBLKR) run(k_apply_wide<R, KIND, REALH, TPT, NBUF>);
+    else run(k_apply<R, KIND, REALH, TPT, NBUF>);
 }
 
 template <typename R, int KIND, bool REALH>
@@ -1098,6 +1116,11 @@ void launch_kind(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, cons
         }
     } else {
         switch (cfg.tpt) {
+            case 8:
+                // 8 columns per thread only for rank-staged rows (one or two resident
+                // CTAs per SM: more independent gathers per thread instead of more warps)
+                if constexpr (KIND == KBLKR) PS_L(8, 1); else PS_L(4, 1);
+                break;
             case 4: PS_L(4, 1); break;
             case 2: PS_L(2, 1); break;
             default: PS_L(1, 1); break;

@@ -68,8 +68,8 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
         // candidates
         std::vector<LaunchChoice> cand;
         const bool fits = p.I <= 256 && p.S <= 1024;
-        for (int tpt : {1, 2, 4}) {
-            if (fits) {
+        for (int tpt : {1, 2, 4, 8}) {
+            if (fits && tpt < 8) {
                 LaunchChoice c;
                 c.tpt = tpt;
                 c.direct = 1;
@@ -87,12 +87,14 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
                         c.ranked = ranked;
                         const ApplyCfg cfg = apply_config(p, v, dtype, true, &c);
                         // not realisable, or the layout does not fit in shared memory
-                        if (cfg.nbuf != nbuf || cfg.nsplit != ns || (int)cfg.ranked != ranked) continue;
+                        if (cfg.nbuf != nbuf || cfg.nsplit != ns || (int)cfg.ranked != ranked || cfg.tpt != tpt)
+                            continue;
+                        if (tpt == 8 && nbuf != 1) continue;
                         if (cfg.smem > 226 * 1024) continue;
                         cand.push_back(c);
                     }
         }
-        const int limit = env_or("PAULISIM_TUNE_MAX", 64);
+        const int limit = env_or("PAULISIM_TUNE_MAX", 96);
         if ((int)cand.size() > limit) cand.resize(limit);
         // scratch states and the largest split buffer any candidate needs
         const size_t es = dtype == PAULI_C64 ? 8 : 16;
@@ -151,8 +153,9 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
         PS_CHECK(H->n == s->v.n, PAULI_EINVAL, "operator and sector have different qubit counts");
         PS_CHECK(dtype == PAULI_C64 || dtype == PAULI_C128, PAULI_EINVAL, "bad dtype");
         PS_CHECK(cfg != nullptr, PAULI_EINVAL, "cfg is NULL");
-        PS_CHECK(cfg->cols_per_thread == 1 || cfg->cols_per_thread == 2 || cfg->cols_per_thread == 4,
-                 PAULI_EINVAL, "cols_per_thread must be 1, 2 or 4");
+        PS_CHECK(cfg->cols_per_thread == 1 || cfg->cols_per_thread == 2 || cfg->cols_per_thread == 4 ||
+                     cfg->cols_per_thread == 8,
+                 PAULI_EINVAL, "cols_per_thread must be 1, 2, 4 or 8");
         PS_CHECK(cfg->staged_rows == 1 || cfg->staged_rows == 2, PAULI_EINVAL, "staged_rows must be 1 or 2");
         PS_CHECK(cfg->row_split >= 1 && cfg->row_split <= 16, PAULI_EINVAL, "row_split must be in 1..16");
         PS_CHECK(cfg->direct == 0 || cfg->direct == 1, PAULI_EINVAL, "direct must be 0 or 1");
