@@ -311,14 +311,17 @@ int pauli_mlp_destroy(pauli_mlp *m);
  * columns (targets) per thread, staged source rows in flight, piece ranges a
  * row is split into (their partial vectors are added in a fixed order),
  * direct gather (operators small enough to keep whole in shared memory) vs
- * staged source rows, and (single-block sectors) rows staged densely by rank
- * with a rank table vs by bit pattern.  ms: measured time of one apply (0 if
+ * staged source rows vs, in the full space, passes over local bit sets (each
+ * pass stages 2^13-amplitude chunks that contain every X mask of its groups),
+ * and (single-block sectors) rows staged densely by rank with a rank table vs
+ * by bit pattern.  ms: measured time of one apply (0 if
  * not measured). */
 typedef struct {
     int cols_per_thread;  /* 1, 2 or 4; 8 with rank-staged rows (else used as 4) */
     int staged_rows;      /* 1 or 2 */
     int row_split;        /* 1..16 */
-    int direct;           /* 0 or 1 */
+    int direct;           /* 0 staged rows, 1 direct gather (small operators),
+                             2 full space in passes over local bit sets (lattice operators) */
     int ranked;           /* 0 or 1 */
     double ms;
 } pauli_launch_config;

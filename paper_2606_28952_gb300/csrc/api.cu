@@ -154,6 +154,10 @@ void check_integrals(int norb, const double *h, const double *g) {
 
 Plan &ensure_plan(pauli_sum *H, const pauli_sector *s, cudaStream_t st, bool need_partials) {
     Plan &p = get_plan(H, s->v.n_lo, st);
+    if (s->v.kind == PAULI_SECTOR_FULL && !p.local_tried) {
+        p.local_tried = true;
+        p.local = build_local_plan(H, s->v.n, st);
+    }
     // partial vectors of split launches (the split count depends on the dtype)
     const int64_t split_bytes = std::max(apply_split_elems(p, s->v, PAULI_C64) * 8,
                                          apply_split_elems(p, s->v, PAULI_C128) * 16);

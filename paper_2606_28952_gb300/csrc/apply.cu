@@ -397,6 +397,23 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     c.nbuf = nbuf;
     c.smem = nbuf * bb + extra;
     c.base_nct = make_geom(v, tpt * kThreads).cta_off[v.nblk];
+    // full space with a local-pass plan (lattice operators, 2^21 amplitudes or more):
+    // chunks staged in shared memory, one pass per local bit set
+    if (v.kind == PAULI_SECTOR_FULL && p.local) {
+        const int dflt_local = env_int("PAULISIM_LOCAL", v.n >= 21 ? 1 : 0);
+        if (ch.direct >= 0 ? ch.direct == 2 : dflt_local != 0) {
+            c.local = true;
+            c.direct = false;
+            c.smem = 0;
+            c.nbuf = 1;
+            c.nsplit = 1;
+            c.split_p0.assign(2, 0);
+            c.split_p0[1] = (int32_t)p.P;
+            c.nct = local_last_chunks(p.local);
+            c.combine_nct = 0;
+            return c;
+        }
+    }
     // small operators (lattice models): the whole folded plan fits in shared
     // memory and rows have few pieces, so gather straight from global memory
     const bool fits = p.I <= kDirectItems && p.S <= kDirectSegs;
@@ -439,6 +456,7 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
 
 int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow_split, const LaunchChoice *force) {
     const ApplyCfg c = apply_config(p, v, dtype, allow_split, force);
+    if (c.local) return c.nct;  // the last pass writes the partials
     return c.nsplit > 1 ? c.combine_nct : c.base_nct;
 }
 
@@ -453,6 +471,10 @@ void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *
     const ApplyCfg cfg = apply_config(p, v, dtype, allow_split, force);
     if (cfg.nct == 0) return;
     PS_CHECK(cfg.nct < (1ll << 31), PAULI_EUNSUPPORTED, "apply: too many thread blocks");
+    if (cfg.local) {
+        launch_local(p.local, psi_in, psi_out, dtype, v.dim, partials, st);
+        return;
+    }
     PS_CHECK(cfg.smem <= kMaxDynSmem, PAULI_EUNSUPPORTED,
              "apply: the low half of the sector split is too wide for shared-memory staging");
     void *split_buf = nullptr;

@@ -784,26 +784,39 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
     }
     __syncthreads();
     // phase 2: gather from global memory
+    const bool full_tile = rc.c0 + (int64_t)TPT * kThreads <= rc.dlo;  // every column of the tile exists
     for (int it = 0; it < p.I; ++it) {
         const DItem e = sm_it[it];
         if (e.klo < 0) continue;
         uint32_t s[TPT];
         C2 amp[TPT];
+        if (KIND == KFULL) {
+            // full space: the source row is contiguous; 32-bit offsets into it
+            const C2 *src = psi + e.base;
 #pragma unroll
-        for (int j = 0; j < TPT; ++j) {
-            s[j] = tlo[j] ^ e.xlo;
-            int64_t idx;
-            bool ok = act[j];
-            if (KIND == KFULL) {
-                idx = e.base + s[j];
-            } else {
-                ok = ok && (__popc(s[j]) == e.klo);
-                idx = e.base + (ok ? (int64_t)__ldg(v.rank_lo + s[j]) : 0);
+            for (int j = 0; j < TPT; ++j) {
+                s[j] = tlo[j] ^ e.xlo;
+                amp[j] = src[s[j]];
             }
-            amp[j] = psi[idx];
-            if (!ok) {
-                amp[j].x = R(0);
-                amp[j].y = R(0);
+            if (!full_tile) {
+#pragma unroll
+                for (int j = 0; j < TPT; ++j)
+                    if (!act[j]) {
+                        amp[j].x = R(0);
+                        amp[j].y = R(0);
+                    }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                s[j] = tlo[j] ^ e.xlo;
+                const bool ok = act[j] && (__popc(s[j]) == e.klo);
+                const int64_t idx = e.base + (ok ? (int64_t)__ldg(v.rank_lo + s[j]) : 0);
+                amp[j] = psi[idx];
+                if (!ok) {
+                    amp[j].x = R(0);
+                    amp[j].y = R(0);
+                }
             }
         }
         R fr[TPT], fi[TPT];

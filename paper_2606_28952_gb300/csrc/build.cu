@@ -469,6 +469,7 @@ void free_plan(const Allocator &al, Plan &p) {
     dev_free(al, p.s_zlo); dev_free(al, p.s_t0);
     dev_free(al, p.t_zhi); dev_free(al, p.t_c64); dev_free(al, p.t_c32);
     dev_free(al, p.diag_tab64); dev_free(al, p.diag_tab32); dev_free(al, p.diag_rest);
+    free_local_plan(p.local);
     dev_free(al, p.partials);
     dev_free(al, p.split_buf);
     p = Plan();

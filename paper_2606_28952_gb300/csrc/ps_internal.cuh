@@ -121,6 +121,8 @@ struct TunedEntry {
 //               at most kItemsPerPiece items and kSegsPerPiece segments
 //   item i    : one group, or a slice of a group's segments
 //   segment s : terms of one group with equal z_lo, sorted by (z_lo, z_hi)
+struct LocalPlan;  // local.cu
+
 struct Plan {
     int n_lo = -1;
     int64_t G = 0, S = 0, M = 0;      // groups, segments, terms
@@ -153,9 +155,20 @@ struct Plan {
     // partial vectors of split launches (bytes)
     void *split_buf = nullptr;
     int64_t split_cap = 0;
+    // full-space passes over local bit sets (built on first use with a full sector)
+    LocalPlan *local = nullptr;
+    bool local_tried = false;
 };
 
 constexpr int kDiagTabBits = 12;
+
+// Full-space apply in passes over local bit sets (local.cu): 2^kLocBits amplitudes
+// per chunk, the kLocRun lowest bits always local (runs of 8 contiguous amplitudes).
+constexpr int kLocBits = 13;
+constexpr int kLocRun = 3;
+constexpr int kLocMaxPass = 4;
+constexpr int kLocMaxTerms = 2048;
+constexpr int kLocMaxGroups = 512;
 
 // Pairs {t, t ^ x} of a single-group rotation on a single-block sector with both
 // members in the block, each listed once (the member with the lowest bit of x
@@ -256,6 +269,7 @@ struct ApplyCfg {
     int64_t nct = 0;        // CTAs of the gather launch = base_nct * nsplit
     int64_t combine_nct = 0;
     bool direct = false;    // small plan: k_apply_direct (no staging, no split)
+    bool local = false;     // full space: passes over local bit sets (local.cu)
     bool ranked = false;    // single block, rows staged by rank (KBLKR)
 };
 ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split,
@@ -273,6 +287,13 @@ void launch_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi,
 // <lam|G|phi> into result[0..1] (device), then phi, lam <- exp(-i theta G) phi, lam
 void launch_rotate_adjoint(pauli_sum *G, const pauli_sector *s, double theta, void *phi, void *lam, int dtype,
                            double *result, cudaStream_t st);
+
+// local.cu
+LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st);
+void free_local_plan(LocalPlan *lp);
+int64_t local_last_chunks(const LocalPlan *lp);
+int local_passes(const LocalPlan *lp);
+void launch_local(LocalPlan *lp, const void *in, void *out, int dtype, int64_t dim, double *partials, cudaStream_t st);
 
 // linalg.cu: per-device scratch of FP64 partial sums shared by the reductions
 // that run on a fixed grid (pauli_vdot, pauli_rotate_adjoint)

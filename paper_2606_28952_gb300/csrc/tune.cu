@@ -43,7 +43,7 @@ pauli_launch_config to_public(const ApplyCfg &c, double ms) {
     o.cols_per_thread = c.tpt;
     o.staged_rows = c.nbuf;
     o.row_split = c.nsplit;
-    o.direct = c.direct ? 1 : 0;
+    o.direct = c.local ? 2 : (c.direct ? 1 : 0);
     o.ranked = c.ranked ? 1 : 0;
     o.ms = ms;
     return o;
@@ -65,9 +65,18 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
         cudaStream_t cs = (cudaStream_t)st;
         Plan &p = get_plan(H, s->v.n_lo, cs);
         const SectorView &v = s->v;
+        if (v.kind == PAULI_SECTOR_FULL && !p.local_tried) {
+            p.local_tried = true;
+            p.local = build_local_plan(H, v.n, cs);
+        }
         // candidates
         std::vector<LaunchChoice> cand;
         const bool fits = p.I <= 256 && p.S <= 1024;
+        if (s->v.kind == PAULI_SECTOR_FULL && p.local) {
+            LaunchChoice c;
+            c.direct = 2;
+            cand.push_back(c);
+        }
         for (int tpt : {1, 2, 4, 8}) {
             if (fits && tpt < 8) {
                 LaunchChoice c;
@@ -158,12 +167,16 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
                  PAULI_EINVAL, "cols_per_thread must be 1, 2, 4 or 8");
         PS_CHECK(cfg->staged_rows == 1 || cfg->staged_rows == 2, PAULI_EINVAL, "staged_rows must be 1 or 2");
         PS_CHECK(cfg->row_split >= 1 && cfg->row_split <= 16, PAULI_EINVAL, "row_split must be in 1..16");
-        PS_CHECK(cfg->direct == 0 || cfg->direct == 1, PAULI_EINVAL, "direct must be 0 or 1");
+        PS_CHECK(cfg->direct == 0 || cfg->direct == 1 || cfg->direct == 2, PAULI_EINVAL, "direct must be 0, 1 or 2");
         PS_CHECK(cfg->ranked == 0 || cfg->ranked == 1, PAULI_EINVAL, "ranked must be 0 or 1");
         cudaStream_t cs = nullptr;
         PS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         try {
             Plan &p = get_plan(H, s->v.n_lo, cs);
+            if (s->v.kind == PAULI_SECTOR_FULL && !p.local_tried) {
+                p.local_tried = true;
+                p.local = build_local_plan(H, s->v.n, cs);
+            }
             LaunchChoice c;
             c.tpt = cfg->cols_per_thread;
             c.nbuf = cfg->staged_rows;

@@ -126,6 +126,84 @@ def test_apply_direct_diagonal_table(ps, dt, n_lo):
         assert abs(complex(r[0], r[1]) - e_ref) <= TOL[dt] * np.linalg.norm(ref) * np.linalg.norm(psi)
 
 
+def _lattice_terms(n, seed):
+    """Complex sum of short-range groups (bit pairs at distance 1..3, 2-4 terms with
+    z anywhere) and a diagonal group of 50 random Z strings."""
+    rng = np.random.default_rng(seed)
+    xs, zs, cre, cim = [], [], [], []
+    for _ in range(50):
+        xs.append(0)
+        zs.append(int(rng.integers(1, 1 << n)))
+        cre.append(rng.normal())
+        cim.append(0.2 * rng.normal())
+    for a, d in zip(rng.integers(0, n - 1, 30), rng.integers(1, 4, 30)):
+        xm = (1 << int(a)) | (1 << min(int(a) + int(d), n - 1))
+        for _ in range(int(rng.integers(2, 5))):
+            xs.append(xm)
+            zs.append(int(rng.integers(0, 1 << n)))
+            cre.append(rng.normal())
+            cim.append(rng.normal())
+    return (np.array(xs, np.uint64), np.array(zs, np.uint64), np.array(cre), np.array(cim))
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("case", ["xxz16", "lattice17"])
+def test_apply_local_passes(ps, dt, case):
+    """The full space in passes over local bit sets (2 passes here, forced at this
+    size): apply and expect against the oracle, with and without the H psi output."""
+    import torch
+    if case == "xxz16":
+        n = 16
+        x_, z_, cre, cim = w.xxz_terms(n, 1)
+        H = ps.PauliSum.from_terms(n, x_, z_, cre, cim)
+        R = oracle.build_sum(n, x_, z_, None, cre, cim)
+    else:
+        n = 17
+        x_, z_, cre, cim = _lattice_terms(n, 5)
+        H = ps.PauliSum.from_terms(n, x_, z_, cre, cim, form=ps.XZ)
+        R = oracle.build_sum(n, x_, z_, None, cre, cim, letter_form=False)
+    S = ps.Sector.full(n)
+    So = oracle.Sector.full(n)
+    ps.prepare(H, S)
+    c = ps.LaunchConfig(cols_per_thread=1, staged_rows=1, row_split=1, direct=2, ranked=0, ms=0.0)
+    ps.set_launch_config(H, S, _tdt(dt), c)
+    assert ps.launch_config(H, S, _tdt(dt))["direct"] == 2
+    psi = w.random_state(1 << n, 23)
+    x = _to_dev(psi, dt)
+    xin = x.cpu().numpy().astype(np.complex128)
+    ref = oracle.apply(So, R, xin)
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    assert _rel(out, ref) <= TOL[dt]
+    e_ref = np.vdot(xin, ref)
+    for hp in (None, torch.empty_like(x)):
+        r = ps.expect(H, S, x, hpsi_out=hp).cpu().numpy()
+        assert abs(complex(r[0], r[1]) - e_ref) <= TOL[dt] * np.linalg.norm(ref) * np.linalg.norm(xin)
+        assert abs(r[2] - np.linalg.norm(ref) ** 2) <= 10 * TOL[dt] * np.linalg.norm(ref) ** 2
+        if hp is not None:
+            assert _rel(hp.cpu().numpy().astype(np.complex128), ref) <= TOL[dt]
+
+
+def test_apply_local_passes_24_sites_default(ps):
+    """At 24 sites the pass scheme is the default launch of the full space (3 passes
+    for the open chain); sampled rows against the per-row oracle."""
+    n = 24
+    x_, z_, cre, cim = w.xxz_terms(n, 1)
+    H = ps.PauliSum.from_terms(n, x_, z_, cre, cim)
+    R = oracle.build_sum(n, x_, z_, None, cre, cim)
+    S = ps.Sector.full(n)
+    So = oracle.Sector.full(n)
+    psi = w.random_state(1 << n, 29)
+    x = _to_dev(psi, "c64")
+    out = ps.apply(H, S, x)
+    assert ps.launch_config(H, S)["direct"] == 2
+    rows = np.random.default_rng(1).integers(0, 1 << n, 300)
+    rows = np.concatenate([rows, [0, 1, 7, 8, (1 << n) - 1]])
+    ref = oracle.apply_rows(So, R, x.cpu().numpy().astype(np.complex128), rows)
+    got = out.cpu().numpy().astype(np.complex128)[rows]
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, scale) * 10
+
+
 @pytest.mark.parametrize("dt", ["c128", "c64"])
 def test_apply_multiblock_sz0_xxz(ps, dt):
     """Open XXZ chain, 14 sites, Sz = 0 as 8 product blocks (k, 7-k) of a 7|7 split."""
