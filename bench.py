@@ -404,8 +404,8 @@ def run_xxz(args, rank, world, local_rank):
         S = ps.Sector.full(n, args.n_lo or 10)
         label = f"xxz{n} full space 2^{n}, split {S.n_lo if S.n_lo else 10}|{n - (args.n_lo or 10)}"
     else:
-        nl = args.n_lo or 12
-        S = ps.Sector(n, ps.BLOCKS, nl, [(k, n // 2 - k) for k in range(0, min(nl, n // 2) + 1)])
+        nl = args.n_lo or 15  # 15|15: 16 blocks (k, 15-k); fastest split measured for this chain
+        S = ps.Sector(n, ps.BLOCKS, nl, [(k, n // 2 - k) for k in range(0, min(nl, n // 2) + 1) if n // 2 - k <= n - nl])
         label = f"xxz{n} Sz=0 blocks, split {nl}|{n - nl}, D={S.dim}"
     ps.prepare(H, S)
     xc, _, _ = H.export()
