@@ -94,6 +94,17 @@ def profiled_traffic(name: str):
     return d["dram_bytes_per_launch"] if h.hexdigest() == d["sources_sha256"] else None
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over the ranks of the default process group (x itself
+    without one): the job's step time is that of its slowest replica."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -255,11 +266,7 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     times_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_step = sum(times_ms) / len(times_ms) / 1e3
-    if dist:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = tt.item()
+    t_step = max_over_ranks(sum(times_ms) / len(times_ms) / 1e3, dist, dev)
     value = world * U / t_step
 
     # end to end: pinned host psi -> device -> apply -> host, every step
