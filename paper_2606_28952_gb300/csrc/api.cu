@@ -158,7 +158,8 @@ Plan &ensure_plan(pauli_sum *H, const pauli_sector *s, cudaStream_t st, bool nee
         p.local_tried = true;
         p.local = build_local_plan(H, s->v.n, st);
     }
-    // partial vectors of split launches (the split count depends on the dtype)
+    // partial vectors of split launches (the split count depends on the dtype:
+    // sized for both, so that either precision can run on the same plan)
     const int64_t split_bytes = std::max(apply_split_elems(p, s->v, PAULI_C64) * 8,
                                          apply_split_elems(p, s->v, PAULI_C128) * 16);
     if (p.split_cap < split_bytes) {
@@ -170,8 +171,11 @@ Plan &ensure_plan(pauli_sum *H, const pauli_sector *s, cudaStream_t st, bool nee
         p.split_cap = split_bytes;
     }
     if (need_partials) {
-        const int64_t nct = std::max(apply_num_ctas(p, s->v, PAULI_C128, true),
-                                     apply_num_ctas(p, s->v, PAULI_C128, false));
+        // one 4-double slot per CTA that writes partials, for either precision (their
+        // launch shapes differ, e.g. a split in complex64 only) and either split mode
+        int64_t nct = 0;
+        for (int dt : {PAULI_C64, PAULI_C128})
+            for (bool split : {true, false}) nct = std::max(nct, apply_num_ctas(p, s->v, dt, split));
         if (p.partials_cap < nct) {
             PS_CUDA(cudaStreamSynchronize(st));
             dev_free(H->al, p.partials);
@@ -501,6 +505,8 @@ int pauli_expect(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype
             PS_CUDA(cudaMemsetAsync(result, 0, 4 * sizeof(double), cs));
             return;
         }
+        PS_CHECK(p.partials != nullptr && nct <= p.partials_cap, PAULI_EINVAL,
+                 "expect: the plan's partial-sum buffer is too small (internal)");
         launch_apply(H, p, s->v, psi, hpsi_out, dtype, p.partials, cs);
         launch_reduce(p.partials, nct, result, cs);
     });

@@ -312,6 +312,8 @@ void krylov_step_t(pauli_krylov *k, void *psi_v, double dt, cudaStream_t st) {
     k_normalize<R><<<nb, kVecThreads, 0, st>>>(psi, V, n, k->sc, 0);
     PS_LAUNCH_CHECK();
     const int64_t nparts = apply_num_ctas(*p, k->s->v, k->dtype, true);
+    PS_CHECK(p->partials != nullptr && nparts <= p->partials_cap, PAULI_EINVAL,
+             "krylov: the plan's partial-sum buffer is too small (internal)");
     for (int j = 0; j < k->m; ++j) {
         C2 *vj = V + (int64_t)j * n;
         C2 *w = V + (int64_t)(j + 1) * n;  // w_j is built in place of v_{j+1}

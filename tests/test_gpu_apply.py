@@ -328,6 +328,29 @@ def test_apply_24_qubits_properties(ps, mol24):
 # ----------------------------------------------------------------------------
 # expectation values
 # ----------------------------------------------------------------------------
+def test_expect_both_precisions_on_one_plan(ps):
+    """13 orbitals, (6a,6b): the complex64 launch splits its rows while the
+    complex128 one does not, so the plan's partial sums must be sized for both
+    (complex128 first, then complex64, then again); the two energies agree."""
+    import torch
+    norb = 13
+    h, g = w.molecular_integrals(norb, 4)
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    S = ps.Sector.molecular(norb, 6, 6)
+    psi = w.random_state(S.dim, 77)
+    x128 = _to_dev(psi, "c128")
+    x64 = _to_dev(psi, "c64")
+    ps.prepare(H, S)
+    cfg64, cfg128 = ps.launch_config(H, S, torch.complex64), ps.launch_config(H, S, torch.complex128)
+    assert cfg64["row_split"] > 1 and cfg128["row_split"] == 1
+    e = []
+    for x in (x128, x64, x128, x64):
+        r = ps.expect(H, S, x, hpsi_out=torch.empty_like(x)).cpu().numpy()
+        e.append(r[0])
+    assert abs(e[0] - e[2]) == 0.0 and abs(e[1] - e[3]) == 0.0  # fixed reduction order
+    assert abs(e[0] - e[1]) <= 1e-6 * max(1.0, abs(e[0]))
+
+
 @pytest.mark.parametrize("dt", ["c128", "c64"])
 def test_expect_matches_oracle_and_hf(ps, dt):
     h, g, R = _mol(6, 3, 3)
