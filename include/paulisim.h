@@ -313,6 +313,9 @@ int pauli_mlp_destroy(pauli_mlp *m);
  * direct gather (operators small enough to keep whole in shared memory) vs
  * staged source rows vs, in the full space, passes over local bit sets (each
  * pass stages 2^13-amplitude chunks that contain every X mask of its groups),
+ * vs, in a single-block sector with a low half of at most 12 qubits, a gather
+ * over per-item lists of the (target, source) pairs that stay in the block
+ * (one thread block per row, warp-private accumulator rows in shared memory),
  * and (single-block sectors) rows staged densely by rank with a rank table vs
  * by bit pattern.  ms: measured time of one apply (0 if
  * not measured). */
@@ -321,7 +324,8 @@ typedef struct {
     int staged_rows;      /* 1 or 2 */
     int row_split;        /* 1..16 */
     int direct;           /* 0 staged rows, 1 direct gather (small operators),
-                             2 full space in passes over local bit sets (lattice operators) */
+                             2 full space in passes over local bit sets (lattice operators),
+                             3 lists of valid pairs (single block, low half <= 12 qubits) */
     int ranked;           /* 0 or 1 */
     double ms;
 } pauli_launch_config;

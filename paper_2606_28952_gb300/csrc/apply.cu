@@ -414,11 +414,29 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
             return c;
         }
     }
+    // a single block with a low half of at most kListMaxLo qubits: gather over
+    // the lists of valid (target, source) pairs, one CTA per row (list.cu)
+    const std::vector<int64_t> *cumw = &p.h_pc_cumw;
+    const ListTab *lt = single ? find_lists(p, v.klo[0]) : nullptr;
+    bool use_list = false;
+    if (lt) {
+        const int dflt_list = env_int("PAULISIM_LIST", (dtype == PAULI_C128 && v.dlo[0] >= 384) ? 1 : 0);
+        use_list = ch.direct >= 0 ? ch.direct == 3 : dflt_list != 0;
+    }
+    if (use_list) {
+        c.list = true;
+        c.ranked = false;
+        c.tpt = 1;
+        c.nbuf = 1;
+        c.smem = list_smem(dtype, v.dlo[0]);
+        c.base_nct = v.dlo[0] > 0 ? v.dhi[0] : 0;
+        cumw = &lt->h_pc_cumw;
+    }
     // small operators (lattice models): the whole folded plan fits in shared
     // memory and rows have few pieces, so gather straight from global memory
     const bool fits = p.I <= kDirectItems && p.S <= kDirectSegs;
     const int dflt_direct = env_int("PAULISIM_DIRECT", fits ? 1 : 0);
-    c.direct = fits && (ch.direct >= 0 ? ch.direct != 0 : dflt_direct != 0);
+    c.direct = !use_list && fits && (ch.direct >= 0 ? ch.direct == 1 : dflt_direct != 0);
     if (c.direct) {
         c.smem = 0;
         c.nbuf = 1;
@@ -444,10 +462,10 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     }
     c.nsplit = nsplit;
     c.split_p0.assign(nsplit + 1, 0);
-    const int64_t W = p.h_pc_cumw.empty() ? 0 : p.h_pc_cumw.back();
+    const int64_t W = cumw->empty() ? 0 : cumw->back();
     for (int k = 1; k < nsplit; ++k) {
         const int64_t target = W * k / nsplit;
-        const int32_t q = (int32_t)(std::lower_bound(p.h_pc_cumw.begin(), p.h_pc_cumw.end(), target) - p.h_pc_cumw.begin());
+        const int32_t q = (int32_t)(std::lower_bound(cumw->begin(), cumw->end(), target) - cumw->begin());
         c.split_p0[k] = std::max(c.split_p0[k - 1], std::min<int32_t>(q, (int32_t)p.P));
     }
     c.split_p0[nsplit] = (int32_t)p.P;
@@ -485,6 +503,10 @@ void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *
         PS_CHECK(p.split_buf != nullptr && p.split_cap >= need, PAULI_EINVAL,
                  "apply: the plan's split buffer is missing (internal)");
         split_buf = p.split_buf;
+    }
+    if (cfg.list) {
+        launch_list(cfg, p, v, psi_in, psi_out, dtype, partials, split_buf, st);
+        return;
     }
     if (dtype == PAULI_C64) launch_apply_f32(cfg, p, v, psi_in, psi_out, partials, split_buf, st);
     else launch_apply_f64(cfg, p, v, psi_in, psi_out, partials, split_buf, st);

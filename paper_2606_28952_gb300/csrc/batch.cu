@@ -111,7 +111,7 @@ void build_descs(pauli_batch *b, int tpt) {
     for (int q = 0; q < b->n; ++q) {
         const int i = b->order[q];
         const SectorView &v = b->S[i]->v;
-        Plan *p = find_plan(b->H[i], v.n_lo);
+        Plan *p = find_plan(b->H[i], v);
         PS_CHECK(p != nullptr, PAULI_EINVAL, "batched apply: a plan is missing (internal)");
         BatchDesc d;
         d.v = v;

@@ -218,25 +218,53 @@ __global__ void k_fill_group_id(int64_t G, const int64_t *gstart, int64_t *gid) 
     for (int64_t t = gstart[g]; t < gstart[g + 1]; ++t) gid[t] = g;
 }
 
+// Low Z mask of a term in a merged plan.  When a target t and its source
+// s = t ^ x have the same low-half popcount (both in one block of a
+// single-block sector), exactly half of the bits of x_lo are set in s, so
+// (-1)^popc((z ^ x_lo) & s) = (-1)^(popc(x_lo) / 2) (-1)^popc(z & s) on every
+// pair the sector keeps: the masks z_lo and z_lo ^ x_lo merge into one segment
+// (the smaller of the two) with that sign on the other's coefficients.  For an
+// odd popc(x_lo) no pair stays in the block; its terms are left as they are.
+__device__ __forceinline__ uint64_t merged_zlo(uint64_t zlo, uint64_t xlo, bool merge, bool &neg) {
+    neg = false;
+    if (!merge || (__popcll(xlo) & 1)) return zlo;
+    const uint64_t alt = zlo ^ xlo;
+    if (alt < zlo) {
+        neg = (__popcll(xlo) >> 1) & 1;
+        return alt;
+    }
+    return zlo;
+}
+
 // sort key of a term inside the plan: (group id, z_lo, z_hi)
-__global__ void k_plan_keys(int64_t m, int n_lo, int n_hi, const int64_t *gid, const uint64_t *z,
-                            uint64_t *khi, uint64_t *klo) {
+__global__ void k_plan_keys(int64_t m, int n_lo, int n_hi, const int64_t *gid, const uint64_t *x, const uint64_t *z,
+                            int merge, uint64_t *khi, uint64_t *klo) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     uint64_t lomask = (n_lo >= 64) ? ~0ull : ((1ull << n_lo) - 1ull);
-    uint64_t zlo = z[i] & lomask;
+    bool neg;
+    uint64_t zlo = merged_zlo(z[i] & lomask, x[i] & lomask, merge != 0, neg);
     uint64_t zhi = z[i] >> n_lo;
     khi[i] = (uint64_t)gid[i];
     klo[i] = (zlo << n_hi) | zhi;
 }
 
-__global__ void k_plan_terms(int64_t m, int n_hi, const uint64_t *klo, const int64_t *perm,
-                             const double2 *c, uint32_t *t_zhi, double2 *t_c64, float2 *t_c32) {
+__global__ void k_plan_terms(int64_t m, int n_lo, int n_hi, const uint64_t *klo, const int64_t *perm,
+                             const uint64_t *x, const uint64_t *z, int merge, const double2 *c, uint32_t *t_zhi,
+                             double2 *t_c64, float2 *t_c32) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     uint64_t hmask = (n_hi >= 64) ? ~0ull : ((1ull << n_hi) - 1ull);
+    uint64_t lomask = (n_lo >= 64) ? ~0ull : ((1ull << n_lo) - 1ull);
     t_zhi[i] = (uint32_t)(klo[i] & hmask);
-    double2 v = c[perm[i]];
+    const int64_t o = perm[i];
+    double2 v = c[o];
+    bool neg;
+    (void)merged_zlo(z[o] & lomask, x[o] & lomask, merge != 0, neg);
+    if (neg) {
+        v.x = -v.x;
+        v.y = -v.y;
+    }
     t_c64[i] = v;
     t_c32[i] = make_float2((float)v.x, (float)v.y);
 }
@@ -470,20 +498,24 @@ void free_plan(const Allocator &al, Plan &p) {
     dev_free(al, p.t_zhi); dev_free(al, p.t_c64); dev_free(al, p.t_c32);
     dev_free(al, p.diag_tab64); dev_free(al, p.diag_tab32); dev_free(al, p.diag_rest);
     free_local_plan(p.local);
+    free_lists(al, p);
     dev_free(al, p.partials);
     dev_free(al, p.split_buf);
     p = Plan();
 }
 
-Plan *find_plan(pauli_sum *h, int n_lo) {
+Plan *find_plan(pauli_sum *h, const SectorView &v) {
+    const bool merged = plan_merges(v);
     for (int i = 0; i < h->nplans; ++i)
-        if (h->plans[i].n_lo == n_lo) return &h->plans[i];
+        if (h->plans[i].n_lo == v.n_lo && h->plans[i].merged == merged) return &h->plans[i];
     return nullptr;
 }
 
-Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
+Plan &get_plan(pauli_sum *h, const SectorView &v, cudaStream_t st) {
+    const int n_lo = v.n_lo;
+    const bool merged = plan_merges(v);
     for (int i = 0; i < h->nplans; ++i)
-        if (h->plans[i].n_lo == n_lo) return h->plans[i];
+        if (h->plans[i].n_lo == n_lo && h->plans[i].merged == merged) return h->plans[i];
     if (h->nplans == 4) {  // evict the oldest
         free_plan(h->al, h->plans[0]);
         for (int i = 1; i < 4; ++i) h->plans[i - 1] = h->plans[i];
@@ -495,6 +527,7 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
     const int64_t M = h->m, G = h->G;
     Plan p;
     p.n_lo = n_lo;
+    p.merged = merged;
     p.M = M;
     p.G = G;
     p.real = h->real;
@@ -508,12 +541,13 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
         DevBuf<uint64_t> khi(al, M), klo(al, M), seg_key(al, M);
         k_fill_group_id<<<nblk(G), 256, 0, st>>>(G, h->gstart, gid.p);
         PS_LAUNCH_CHECK();
-        k_plan_keys<<<nblk(M), 256, 0, st>>>(M, n_lo, n_hi, gid.p, h->z, khi.p, klo.p);
+        k_plan_keys<<<nblk(M), 256, 0, st>>>(M, n_lo, n_hi, gid.p, h->x, h->z, merged ? 1 : 0, khi.p, klo.p);
         PS_LAUNCH_CHECK();
         int gbits = 1;
         while ((1ll << gbits) <= G) ++gbits;
         radix_sort_keys(khi.p, klo.p, perm.p, M, gbits, h->n, al, st);
-        k_plan_terms<<<nblk(M), 256, 0, st>>>(M, n_hi, klo.p, perm.p, h->c, p.t_zhi, p.t_c64, p.t_c32);
+        k_plan_terms<<<nblk(M), 256, 0, st>>>(M, n_lo, n_hi, klo.p, perm.p, h->x, h->z, merged ? 1 : 0, h->c,
+                                              p.t_zhi, p.t_c64, p.t_c32);
         PS_LAUNCH_CHECK();
         // segments: runs of equal (group, z_lo) in the re-sorted order
         k_shift_right<<<nblk(M), 256, 0, st>>>(M, klo.p, n_hi, seg_key.p);
@@ -605,6 +639,9 @@ Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st) {
         p.s_xhi = static_cast<uint32_t *>(upload(s_xhi.data(), (S > 0 ? S : 0) * sizeof(uint32_t)));
     }
     p.it_s0 = static_cast<int32_t *>(upload(it_s0.data(), it_s0.size() * sizeof(int32_t)));
+    p.h_it_xlo = it_xlo;
+    p.h_it_s0 = it_s0;
+    p.h_pc_i0 = pc_i0;
     if (p.nseg_diag > 0 && n_lo <= kDiagTabBits) {
         // diagonal table, and the diagonal segments left with a z_hi != 0 term
         const int nd = p.nseg_diag;

@@ -303,7 +303,7 @@ void krylov_step_t(pauli_krylov *k, void *psi_v, double dt, cudaStream_t st) {
     C2 *V = static_cast<C2 *>(k->V);
     const int64_t n = k->dim;
     const int nb = k->vec_blocks;
-    Plan *p = find_plan(k->H, k->s->v.n_lo);
+    Plan *p = find_plan(k->H, k->s->v);
     PS_CHECK(p != nullptr, PAULI_EINVAL, "krylov: operator plan missing");
     double *red = k->sc->red;
     // v_0 = psi / ||psi||

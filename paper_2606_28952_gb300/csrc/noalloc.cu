@@ -67,7 +67,7 @@ extern "C" int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const v
             const char *b = static_cast<const char *>(hpsi_out);
             PS_CHECK(a + bytes <= b || b + bytes <= a, PAULI_EINVAL, "psi and hpsi_out overlap");
         }
-        Plan *p = find_plan(H, s->v.n_lo);
+        Plan *p = find_plan(H, s->v);
         PS_CHECK(p != nullptr, PAULI_EINVAL,
                  "no apply plan for this sector split: call pauli_prepare(H, s) once before pauli_expect_noalloc");
         // one CTA per (row, column tile), no split: the launch touches no scratch but the static array

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <string>
 #include <vector>
@@ -105,7 +106,8 @@ struct LaunchChoice {
     int tpt = 0;      // columns per thread: 1, 2 or 4
     int nbuf = 0;     // staged source rows in flight: 1 or 2
     int nsplit = 0;   // piece ranges per row: 1..16
-    int direct = -1;  // 1: direct gather (small plans), 0: staged
+    int direct = -1;  // 1: direct gather (small plans), 0: staged, 2: local passes (full space),
+                      // 3: per-item lists of valid pairs (single block, n_lo <= kListMaxLo)
     int ranked = -1;  // 1: rows staged by rank + rank table, 0: by bit pattern
 };
 struct TunedEntry {
@@ -123,8 +125,26 @@ struct TunedEntry {
 //   segment s : terms of one group with equal z_lo, sorted by (z_lo, z_hi)
 struct LocalPlan;  // local.cu
 
+// Lists of the valid (target, source) pairs of each distinct x_lo of a plan's
+// items in one single-block sector (low half of k_lo particles, n_lo <=
+// kListMaxLo, D_lo <= kListMaxDlo).  Entry of list l: the pairs of targets t_lo
+// with t_lo ^ x_lo in the block, ascending in the target's rank, each packed as
+// rank(t_lo) | rank(t_lo ^ x_lo) << 10 | t_lo << 20.
+struct ListTab {
+    int klo = -1;
+    int64_t n_list = 0, n_ent = 0;
+    uint32_t *ent = nullptr;     // [n_ent]
+    int32_t *off = nullptr;      // [n_list + 1]
+    int32_t *it_list = nullptr;  // [I] list of each item
+    std::vector<int64_t> h_pc_cumw;  // [P+1] cumulative per-piece work of the list gather
+};
+constexpr int kListMaxLo = 12;
+constexpr int64_t kListMaxDlo = 1024;
+constexpr int kListCache = 2;
+
 struct Plan {
     int n_lo = -1;
+    bool merged = false;               // low Z masks merged for single-block sectors (build.cu)
     int64_t G = 0, S = 0, M = 0;      // groups, segments, terms
     int64_t P = 0, I = 0;             // pieces, items
     int32_t nseg_diag = 0;            // segments [0, nseg_diag) belong to the x = 0 group
@@ -158,6 +178,11 @@ struct Plan {
     // full-space passes over local bit sets (built on first use with a full sector)
     LocalPlan *local = nullptr;
     bool local_tried = false;
+    // host copies of the item tables (list building)
+    std::vector<uint32_t> h_it_xlo;
+    std::vector<int32_t> h_it_s0, h_pc_i0;
+    ListTab lists[kListCache];   // per k_lo of the single-block sectors seen
+    int nlists = 0;
 };
 
 constexpr int kDiagTabBits = 12;
@@ -240,8 +265,18 @@ void jw_fermion_raw_device(int n, int nterms, const int *nf, const int *modes, c
                            const double *cre, const double *cim, const Allocator &al,
                            DevBuf<uint64_t> &x, DevBuf<uint64_t> &z, DevBuf<double2> &c,
                            int64_t &count, cudaStream_t st);
-Plan &get_plan(pauli_sum *h, int n_lo, cudaStream_t st);
-Plan *find_plan(pauli_sum *h, int n_lo);  // existing plan or nullptr; never builds
+// Plans are keyed by (n_lo, merged): a single-block sector uses a plan whose
+// segments merge the low Z masks z_lo and z_lo ^ x_lo (exact on every pair the
+// sector keeps; PAULISIM_MERGE=0 turns it off), other sectors the plain plan.
+inline bool plan_merges(const SectorView &v) {
+    static const int on = [] {
+        const char *e = getenv("PAULISIM_MERGE");
+        return e ? atoi(e) : 1;
+    }();
+    return on != 0 && v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1;
+}
+Plan &get_plan(pauli_sum *h, const SectorView &v, cudaStream_t st);
+Plan *find_plan(pauli_sum *h, const SectorView &v);  // existing plan or nullptr; never builds
 void free_plan(const Allocator &al, Plan &p);
 
 // scan.cu
@@ -271,6 +306,7 @@ struct ApplyCfg {
     bool direct = false;    // small plan: k_apply_direct (no staging, no split)
     bool local = false;     // full space: passes over local bit sets (local.cu)
     bool ranked = false;    // single block, rows staged by rank (KBLKR)
+    bool list = false;      // single block, n_lo <= kListMaxLo: per-item lists of valid pairs (list.cu)
 };
 ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split,
                       const LaunchChoice *force = nullptr);
@@ -287,6 +323,16 @@ void launch_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi,
 // <lam|G|phi> into result[0..1] (device), then phi, lam <- exp(-i theta G) phi, lam
 void launch_rotate_adjoint(pauli_sum *G, const pauli_sector *s, double theta, void *phi, void *lam, int dtype,
                            double *result, cudaStream_t st);
+
+// list.cu
+// Builds what a sector needs beyond the plan: the local-pass plan of a full
+// space, the pair lists of a single-block sector.
+void prepare_for_sector(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t st);
+const ListTab *find_lists(const Plan &p, int klo);
+void free_lists(const Allocator &al, Plan &p);
+size_t list_smem(int dtype, int64_t dlo);
+void launch_list(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out, int dtype,
+                 double *partials, void *split_buf, cudaStream_t st);
 
 // local.cu
 LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st);

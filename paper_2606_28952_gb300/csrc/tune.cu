@@ -43,7 +43,7 @@ pauli_launch_config to_public(const ApplyCfg &c, double ms) {
     o.cols_per_thread = c.tpt;
     o.staged_rows = c.nbuf;
     o.row_split = c.nsplit;
-    o.direct = c.local ? 2 : (c.direct ? 1 : 0);
+    o.direct = c.list ? 3 : (c.local ? 2 : (c.direct ? 1 : 0));
     o.ranked = c.ranked ? 1 : 0;
     o.ms = ms;
     return o;
@@ -63,12 +63,9 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
         PS_CHECK(dtype == PAULI_C64 || dtype == PAULI_C128, PAULI_EINVAL, "bad dtype");
         PS_CHECK(reps >= 1 && reps <= 1000, PAULI_EINVAL, "reps must be in 1..1000");
         cudaStream_t cs = (cudaStream_t)st;
-        Plan &p = get_plan(H, s->v.n_lo, cs);
+        Plan &p = get_plan(H, s->v, cs);
         const SectorView &v = s->v;
-        if (v.kind == PAULI_SECTOR_FULL && !p.local_tried) {
-            p.local_tried = true;
-            p.local = build_local_plan(H, v.n, cs);
-        }
+        prepare_for_sector(H, p, v, cs);
         // candidates
         std::vector<LaunchChoice> cand;
         const bool fits = p.I <= 256 && p.S <= 1024;
@@ -77,6 +74,16 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
             c.direct = 2;
             cand.push_back(c);
         }
+        if (v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1 && find_lists(p, v.klo[0]))
+            for (int ns : {1, 2, 4, 8, 16}) {
+                if (ns > 1 && ns > std::max<int64_t>(1, p.P / 8)) continue;
+                LaunchChoice c;
+                c.direct = 3;
+                c.nsplit = ns;
+                const ApplyCfg cfg = apply_config(p, v, dtype, true, &c);
+                if (!cfg.list || cfg.nsplit != ns || cfg.smem > 226 * 1024) continue;
+                cand.push_back(c);
+            }
         for (int tpt : {1, 2, 4, 8}) {
             if (fits && tpt < 8) {
                 LaunchChoice c;
@@ -167,16 +174,13 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
                  PAULI_EINVAL, "cols_per_thread must be 1, 2, 4 or 8");
         PS_CHECK(cfg->staged_rows == 1 || cfg->staged_rows == 2, PAULI_EINVAL, "staged_rows must be 1 or 2");
         PS_CHECK(cfg->row_split >= 1 && cfg->row_split <= 16, PAULI_EINVAL, "row_split must be in 1..16");
-        PS_CHECK(cfg->direct == 0 || cfg->direct == 1 || cfg->direct == 2, PAULI_EINVAL, "direct must be 0, 1 or 2");
+        PS_CHECK(cfg->direct >= 0 && cfg->direct <= 3, PAULI_EINVAL, "direct must be 0, 1, 2 or 3");
         PS_CHECK(cfg->ranked == 0 || cfg->ranked == 1, PAULI_EINVAL, "ranked must be 0 or 1");
         cudaStream_t cs = nullptr;
         PS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         try {
-            Plan &p = get_plan(H, s->v.n_lo, cs);
-            if (s->v.kind == PAULI_SECTOR_FULL && !p.local_tried) {
-                p.local_tried = true;
-                p.local = build_local_plan(H, s->v.n, cs);
-            }
+            Plan &p = get_plan(H, s->v, cs);
+            prepare_for_sector(H, p, s->v, cs);
             LaunchChoice c;
             c.tpt = cfg->cols_per_thread;
             c.nbuf = cfg->staged_rows;
@@ -209,7 +213,7 @@ int pauli_get_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, paul
         PS_CHECK(s && s->magic == kSectorMagic, PAULI_EINVAL, "not a valid pauli_sector handle");
         PS_CHECK(dtype == PAULI_C64 || dtype == PAULI_C128, PAULI_EINVAL, "bad dtype");
         PS_CHECK(cfg != nullptr, PAULI_EINVAL, "cfg is NULL");
-        Plan *p = find_plan(H, s->v.n_lo);
+        Plan *p = find_plan(H, s->v);
         PS_CHECK(p != nullptr, PAULI_EINVAL, "no plan for this sector split yet: call pauli_prepare first");
         double ms = 0.0;
         for (const TunedEntry &t : p->tuned)

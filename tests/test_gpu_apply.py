@@ -261,6 +261,79 @@ def test_apply_rank_staged_matches_pattern_staged(ps, dt):
         assert abs(complex(r[0], r[1]) - E) <= (1e-12 if dt == "c128" else 1e-6)
 
 
+def _force_list(ps, H, S, dt, split):
+    """Install the list-driven gather (direct = 3) with the given row split."""
+    ps.prepare(H, S)
+    c = ps.LaunchConfig(cols_per_thread=1, staged_rows=1, row_split=split, direct=3, ranked=0, ms=0.0)
+    ps.set_launch_config(H, S, _tdt(dt), c)
+    cfg = ps.launch_config(H, S, _tdt(dt))
+    # the split is capped at one range per eight pieces of the plan
+    assert cfg["direct"] == 3 and 1 <= cfg["row_split"] <= split, cfg
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("norb,na,nb,split", [(6, 3, 3, 1), (8, 4, 4, 2), (7, 2, 5, 1), (10, 5, 5, 4),
+                                              (4, 0, 2, 1), (4, 4, 1, 2)])
+def test_apply_list_gather_molecular(ps, dt, norb, na, nb, split):
+    """The gather over per-item lists of valid (target, source) pairs, forced on
+    single-block sectors (including one-configuration low halves, k_lo = 0 and
+    k_lo = n_lo), against the oracle for apply and expect."""
+    h, g, R = _mol(norb, na, nb)
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    S = ps.Sector.molecular(norb, na, nb)
+    So = oracle.Sector.molecular(norb, na, nb)
+    _force_list(ps, H, S, dt, split)
+    x = _to_dev(w.random_state(S.dim, 200 + norb), dt)
+    xin = x.cpu().numpy().astype(np.complex128)
+    ref = oracle.apply(So, R, xin)
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    scale = max(np.linalg.norm(ref), 1e-3 * np.abs(R.c).sum())
+    assert np.linalg.norm(out - ref) <= TOL[dt] * scale
+    r = ps.expect(H, S, x).cpu().numpy()
+    E, _ = oracle.expect(So, R, xin)
+    assert abs(complex(r[0], r[1]) - E) <= (1e-12 if dt == "c128" else 1e-6) * max(1.0, np.abs(R.c).sum())
+    assert abs(r[2] - np.vdot(ref, ref).real) <= 10 * TOL[dt] * max(np.vdot(ref, ref).real, 1e-6)
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("n,n_lo,blk,split", [(12, 6, (3, 3), 1), (16, 8, (4, 4), 2), (16, 10, (5, 3), 1)])
+def test_apply_list_gather_complex_sum(ps, dt, n, n_lo, blk, split):
+    """Complex coefficients (the non-real path) and X masks that leave the block:
+    items whose x_lo has odd popcount have empty lists."""
+    x_, z_, gam, cre, cim = w.random_pauli_terms(n, 300, 31 + n_lo)
+    H = ps.PauliSum.from_terms(n, x_, z_, cre, cim, gamma=gam)
+    R = oracle.build_sum(n, x_, z_, gam, cre, cim)
+    S = ps.Sector(n, ps.BLOCKS, n_lo, [blk])
+    So = oracle.Sector(n, oracle.BLOCKS, n_lo, [blk])
+    _force_list(ps, H, S, dt, split)
+    x = _to_dev(w.random_state(S.dim, 77), dt)
+    ref = oracle.apply(So, R, x.cpu().numpy().astype(np.complex128))
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    assert _rel(out, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_apply_list_gather_24_qubits(ps, mol24, dt):
+    """The list gather without a split at full size: sampled rows against the
+    oracle, and the whole vector against the staged gather."""
+    h, g, H, R, S, So, psi = mol24
+    x = _to_dev(psi, dt)
+    xin = x.cpu().numpy().astype(np.complex128)
+    H2 = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    _force_list(ps, H2, S, dt, 1)
+    out = ps.apply(H2, S, x).cpu().numpy().astype(np.complex128)
+    rng = np.random.default_rng(6)
+    rows = np.unique(np.concatenate([rng.integers(0, S.dim, 150), [0, 923, 924, S.dim - 1]]))
+    ref = oracle.apply_rows(So, R, xin, rows)
+    assert np.linalg.norm(out[rows] - ref) <= TOL[dt] * 1.5 * np.linalg.norm(ref)
+    H3 = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    ps.prepare(H3, S)
+    c = ps.LaunchConfig(cols_per_thread=4, staged_rows=1, row_split=4, direct=0, ranked=0, ms=0.0)
+    ps.set_launch_config(H3, S, _tdt(dt), c)
+    staged = ps.apply(H3, S, x).cpu().numpy().astype(np.complex128)
+    assert _rel(out, staged) <= 2 * TOL[dt]
+
+
 def test_apply_edge_cases(ps):
     import torch
     # empty operator -> zero vector

@@ -160,3 +160,61 @@ def test_rotate_is_unitary_and_additive(mol12):
     b = oracle.rotate(s, G, 0.7, psi)
     assert np.allclose(a, b, atol=1e-13)
     assert abs(np.linalg.norm(b) - 1.0) < 1e-13
+
+
+def _merge_low_masks(R, n_lo):
+    """Rewrite every term X^x Z^z with popc(x_lo) even as the term on the smaller
+    of z_lo and z_lo ^ x_lo, its coefficient times (-1)^(popc(x_lo)/2) when the
+    mask changed (the segment merge of single-block sectors)."""
+    lo = (1 << n_lo) - 1
+    zs, cs = [], []
+    for xv, zv, cv in zip(R.x.tolist(), R.z.tolist(), R.c.tolist()):
+        xl, zl = xv & lo, zv & lo
+        p = bin(xl).count("1")
+        if p % 2 == 0 and (zl ^ xl) < zl:
+            zv ^= xl
+            cv = cv * (-1) ** (p // 2)
+        zs.append(zv)
+        cs.append(cv)
+    return oracle.canonical(R.n, R.x.copy(), np.array(zs, np.uint64), np.array(cs, np.complex128))
+
+
+@pytest.mark.parametrize("norb,na,nb", [(4, 2, 2), (5, 2, 3), (5, 1, 1)])
+def test_low_mask_merge_is_exact_on_single_block_sectors(norb, na, nb):
+    """On a single-block sector a target t and its source t ^ x share the
+    low-half popcount, so half of the bits of x_lo are set in the source and
+    z_lo ^ x_lo carries the phase of z_lo times (-1)^(popc(x_lo)/2): the merged
+    operator has the same sector projection.  On the full space it differs."""
+    h, g = w.molecular_integrals(norb, 4)
+    R = oracle.jw_hamiltonian(norb, h, g, eps_drop=1e-12)
+    Rm = _merge_low_masks(R, norb)
+    assert Rm.m < R.m
+    So = oracle.Sector.molecular(norb, na, nb)
+    psi = w.random_state(So.dim, 8)
+    a, b = oracle.apply(So, R, psi), oracle.apply(So, Rm, psi)
+    assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(a)
+    Sf = oracle.Sector.full(2 * norb)
+    phi = w.random_state(Sf.dim, 9)
+    assert np.linalg.norm(oracle.apply(Sf, R, phi) - oracle.apply(Sf, Rm, phi)) > 1e-3
+
+
+def test_low_mask_merge_needs_a_single_block():
+    """With blocks of different low popcount an X mask with two low bits can move
+    a target of block (1, 3) to a source in block (3, 1), where half of x_lo is
+    not set in the source: the merged operator differs on that sector."""
+    n, n_lo = 8, 4
+    rng = np.random.default_rng(2)
+    xm = 0b00110011
+    zs = [0, 0b1, 0b10, 0b11, 0b10000, 0b100001]
+    R = oracle.build_sum(n, np.full(len(zs), xm, np.uint64), np.array(zs, np.uint64), None,
+                         rng.normal(size=len(zs)), rng.normal(size=len(zs)), letter_form=False)
+    So = oracle.Sector(n, oracle.BLOCKS, n_lo, [(1, 3), (3, 1), (2, 2)])
+    psi = w.random_state(So.dim, 3)
+    Rm = _merge_low_masks(R, n_lo)
+    assert Rm.m < R.m
+    assert np.linalg.norm(oracle.apply(So, R, psi) - oracle.apply(So, Rm, psi)) > 1e-3
+    # restricted to the single block (2, 2) the two agree
+    S1 = oracle.Sector(n, oracle.BLOCKS, n_lo, [(2, 2)])
+    phi = w.random_state(S1.dim, 4)
+    a, b = oracle.apply(S1, R, phi), oracle.apply(S1, Rm, phi)
+    assert np.linalg.norm(a - b) <= 1e-13 * max(np.linalg.norm(a), 1.0)
