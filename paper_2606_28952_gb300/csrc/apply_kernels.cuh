@@ -67,6 +67,7 @@ struct PlanDev {
     int32_t P, nseg_diag;
     const uint32_t *pc_xhi;
     const int32_t *pc_i0;
+    const uint8_t *pc_lofree;
     const uint32_t *it_xlo;
     const uint32_t *it_xhi;
     const int32_t *it_s0;
@@ -450,6 +451,65 @@ __device__ __forceinline__ void gather_piece(const PlanDev &p, int q, const Buf<
     }
 }
 
+// A piece whose items all have x_lo = 0 (none of the x = 0 group) reads each
+// target's source in the same column of the source row.  Every thread folds
+// the piece's high-half phases into the segment coefficients itself (the same
+// loads across the CTA, served by L1) and reads psi from global memory: no
+// staging and no barrier.  Sources of a full space or of a single block only.
+template <typename R, int KIND, bool REALH, int TPT>
+__device__ __forceinline__ void lofree_piece(const SectorView &v, const PlanDev &p, int q, uint32_t thi,
+                                             const typename Cx<R>::T *__restrict__ psi, int64_t c0,
+                                             const bool (&act)[TPT], const uint32_t (&tlo)[TPT], R (&accr)[TPT],
+                                             R (&acci)[TPT]) {
+    using C2 = typename Cx<R>::T;
+    const uint32_t shi = thi ^ __ldg(p.pc_xhi + q);
+    int64_t base;
+    if (KIND == KFULL) {
+        base = (int64_t)shi << v.n_lo;
+    } else {
+        const int bb = v.blk_of_khi[__popc(shi)];
+        base = v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
+    }
+    C2 amp[TPT];
+    R fr[TPT], fi[TPT];
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) {
+        amp[j].x = R(0);
+        amp[j].y = R(0);
+        if (act[j]) amp[j] = psi[base + c0 + threadIdx.x + j * kThreads];
+        fr[j] = R(0);
+        fi[j] = R(0);
+    }
+    const int s0 = __ldg(p.it_s0 + __ldg(p.pc_i0 + q)), s1 = __ldg(p.it_s0 + __ldg(p.pc_i0 + q + 1));
+    for (int s = s0; s < s1; ++s) {
+        const int t0 = __ldg(p.s_t0 + s), t1 = __ldg(p.s_t0 + s + 1);
+        R ar = R(0), ai = R(0);
+        for (int t = t0; t < t1; ++t) {
+            const C2 c = coef<R>(p, t);
+            const uint32_t par = __popc(__ldg(p.t_zhi + t) & shi);
+            ar += flip(c.x, par);
+            if (!REALH) ai += flip(c.y, par);
+        }
+        const uint32_t z = __ldg(p.s_zlo + s);
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            const uint32_t par = __popc(z & tlo[j]);
+            fr[j] += flip(ar, par);
+            if (!REALH) fi[j] += flip(ai, par);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) {
+        if (REALH) {
+            accr[j] += fr[j] * amp[j].x;
+            acci[j] += fr[j] * amp[j].y;
+        } else {
+            accr[j] += fr[j] * amp[j].x - fi[j] * amp[j].y;
+            acci[j] += fr[j] * amp[j].y + fi[j] * amp[j].x;
+        }
+    }
+}
+
 // One (row, column tile, piece range) work unit of the staged gather; the body
 // of k_apply and of the persistent batched launch.  part4: this unit's 4 FP64
 // expectation partials (flags & 2).
@@ -545,11 +605,15 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
         }
     } else {
         while (q < pend) {
-            stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
-            cp_async_wait<0>();
-            __syncthreads();
-            gather_piece<R, KIND, REALH, TPT>(p, q, B0, klo_req[0], tlo, accr, acci, rt);
-            __syncthreads();
+            if (KIND != KBLKN && __ldg(p.pc_lofree + q)) {
+                lofree_piece<R, KIND, REALH, TPT>(v, p, q, rc.thi, psi, rc.c0, act, tlo, accr, acci);
+            } else {
+                stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
+                cp_async_wait<0>();
+                __syncthreads();
+                gather_piece<R, KIND, REALH, TPT>(p, q, B0, klo_req[0], tlo, accr, acci, rt);
+                __syncthreads();
+            }
             q = next_piece<R, KIND>(v, p, q, rc.thi, pend);
         }
     }
@@ -1072,6 +1136,7 @@ PlanDev plan_dev(const Plan &p) {
     d.nseg_diag = p.nseg_diag;
     d.pc_xhi = p.pc_xhi;
     d.pc_i0 = p.pc_i0;
+    d.pc_lofree = p.pc_lofree;
     d.it_xlo = p.it_xlo;
     d.it_xhi = p.it_xhi;
     d.it_s0 = p.it_s0;

@@ -492,6 +492,7 @@ __global__ void k_diag_table(int n_lo, int nseg, const int32_t *s_t0, const uint
 
 void free_plan(const Allocator &al, Plan &p) {
     dev_free(al, p.pc_xhi); dev_free(al, p.pc_i0); dev_free(al, p.it_xlo); dev_free(al, p.it_s0);
+    dev_free(al, p.pc_lofree);
     dev_free(al, p.it_xhi);
     dev_free(al, p.s_xhi);
     dev_free(al, p.s_zlo); dev_free(al, p.s_t0);
@@ -623,6 +624,15 @@ Plan &get_plan(pauli_sum *h, const SectorView &v, cudaStream_t st) {
         p.h_pc_cumw[q + 1] = p.h_pc_cumw[q] + wq;
     }
     p.nseg_diag = (G > 0 && gx[0] == 0) ? g_s0[1] - g_s0[0] : 0;
+    // pieces whose sources sit in the target's own columns (x_lo = 0 throughout),
+    // without the x = 0 group (its segments keep the staged, compensated path)
+    std::vector<uint8_t> pc_lofree(p.P > 0 ? p.P : 1, 0);
+    for (int64_t q = 0; q < p.P; ++q) {
+        bool lf = true;
+        for (int32_t it = pc_i0[q]; it < pc_i0[q + 1] && lf; ++it)
+            lf = it_xlo[it] == 0 && it_s0[it] >= p.nseg_diag;
+        pc_lofree[q] = lf ? 1 : 0;
+    }
     auto upload = [&](const void *src, size_t bytes) {
         void *d = dev_alloc(al, bytes > 0 ? bytes : 4);
         if (bytes > 0) PS_CUDA(cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
@@ -630,6 +640,7 @@ Plan &get_plan(pauli_sum *h, const SectorView &v, cudaStream_t st) {
     };
     p.pc_xhi = static_cast<uint32_t *>(upload(pc_xhi.data(), pc_xhi.size() * sizeof(uint32_t)));
     p.pc_i0 = static_cast<int32_t *>(upload(pc_i0.data(), pc_i0.size() * sizeof(int32_t)));
+    p.pc_lofree = static_cast<uint8_t *>(upload(pc_lofree.data(), (size_t)p.P * sizeof(uint8_t)));
     p.it_xlo = static_cast<uint32_t *>(upload(it_xlo.data(), it_xlo.size() * sizeof(uint32_t)));
     p.it_xhi = static_cast<uint32_t *>(upload(it_xhi.data(), it_xhi.size() * sizeof(uint32_t)));
     {

@@ -151,6 +151,7 @@ struct Plan {
     bool real = true;                  // every C_k real
     uint32_t *pc_xhi = nullptr;        // [P]
     int32_t *pc_i0 = nullptr;          // [P+1] item range
+    uint8_t *pc_lofree = nullptr;      // [P] 1: every item has x_lo = 0 and none is of the x = 0 group
     uint32_t *it_xlo = nullptr;        // [I]
     uint32_t *it_xhi = nullptr;        // [I] x_hi of the item's group
     int32_t *it_s0 = nullptr;          // [I+1] segment range
