@@ -28,7 +28,10 @@ namespace ps {
 
 namespace {
 
-constexpr int kListWarps = kThreads / 32;
+// 128-thread CTAs: four warp accumulator rows, so that two CTAs fit on an SM
+// even in complex128 and one CTA's staging overlaps the other's gather
+constexpr int kListThreads = 128;
+constexpr int kListWarps = kListThreads / 32;
 constexpr int kListK = 4;                     // list entries per lane in one unit
 constexpr int kListChunk = 32 * kListK;       // entries of one unit
 constexpr int kListTile = (int)kListMaxDlo;   // column tile of the geometry: a whole row
@@ -134,7 +137,7 @@ __device__ __forceinline__ void list_unit(const Buf<R> &B, const int4 e, const u
 }
 
 template <typename R, bool REALH>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kListThreads)
 k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>::T *__restrict__ psi,
              typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
     using C2 = typename Cx<R>::T;
@@ -152,7 +155,7 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
         C2 zz;
         zz.x = R(0);
         zz.y = R(0);
-        for (int i = tid; i < kListWarps * dpad; i += kThreads) acc[i] = zz;
+        for (int i = tid; i < kListWarps * dpad; i += kListThreads) acc[i] = zz;
     }
     C2 *my = acc + (size_t)warp * dpad;
     int unused = 0;
@@ -161,7 +164,7 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
     while (q < pend) {
         stage_piece<R, KBLKR, REALH>(v, p, q, rc.thi, psi, B, &unused);
         const int i0 = __ldg(p.pc_i0 + q), i1 = __ldg(p.pc_i0 + q + 1);
-        for (int it = i0 + tid; it < i1; it += kThreads) {
+        for (int it = i0 + tid; it < i1; it += kListThreads) {
             const int l = __ldg(L.it_list + it);
             const int a = __ldg(L.off + l);
             rng[it - i0] = make_int2(a, __ldg(L.off + l + 1) - a);
@@ -192,7 +195,7 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
 
     // epilogue: the warp rows added in a fixed order; store and / or FP64 reductions
     ExpAcc<R> ea;
-    for (int c = tid; c < dlo; c += kThreads) {
+    for (int c = tid; c < dlo; c += kListThreads) {
         R sr = R(0), si = R(0);
 #pragma unroll
         for (int w = 0; w < kListWarps; ++w) {
@@ -240,7 +243,7 @@ void launch_list_k(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, co
     using C2 = typename Cx<R>::T;
     auto kern = k_apply_list<R, REALH>;
     PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
-    kern<<<(unsigned)cfg.nct, kThreads, cfg.smem, st>>>(v, geo, pd, ld, static_cast<const C2 *>(in),
+    kern<<<(unsigned)cfg.nct, kListThreads, cfg.smem, st>>>(v, geo, pd, ld, static_cast<const C2 *>(in),
                                                          static_cast<C2 *>(out), partials, flags);
     PS_LAUNCH_CHECK();
 }
