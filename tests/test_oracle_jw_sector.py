@@ -190,3 +190,31 @@ def test_full_sector_is_identity():
     assert s.dim == 512
     assert np.array_equal(s.configs(), np.arange(512, dtype=np.uint64))
     assert np.array_equal(s.index(np.arange(512, dtype=np.uint64)), np.arange(512))
+
+
+@pytest.mark.parametrize("n,n_lo,blocks", [(30, 15, [(1, 1), (2, 0), (0, 2)]), (32, 16, [(2, 1), (1, 2)]),
+                                           (34, 17, [(1, 1)])])
+def test_sector_index_by_binary_search_above_28_qubits(n, n_lo, blocks):
+    """Above 28 qubits the oracle finds an index by binary search in the block's
+    sorted list instead of a lookup table.  Pinned against positions in an
+    enumeration written here (blocks in the given order, high string outer,
+    low string inner, both ascending), and against -1 for strings outside."""
+    from itertools import combinations
+    S = oracle.Sector(n, oracle.BLOCKS, n_lo, blocks)
+    n_hi = n - n_lo
+    expect_cfg = []
+    for k_lo, k_hi in blocks:
+        los = sorted(sum(1 << b for b in c) for c in combinations(range(n_lo), k_lo))
+        his = sorted(sum(1 << b for b in c) for c in combinations(range(n_hi), k_hi))
+        expect_cfg += [lo | (hi << n_lo) for hi in his for lo in los]
+    assert S.dim == len(expect_cfg)
+    cfg = np.array(expect_cfg, dtype=np.uint64)
+    assert np.array_equal(S.configs(), cfg)
+    assert np.array_equal(S.index(cfg), np.arange(len(cfg)))
+    # outside: wrong popcounts in either half, and a bit at or above n
+    rng = np.random.default_rng(n)
+    inside = set(expect_cfg)
+    probes = [0, 1, (1 << n_lo) | 1 | 2 | 4, (1 << n) - 1, 1 << n, (1 << n) | int(cfg[0])]
+    probes += [int(b) for b in rng.integers(0, 1 << n, 200, dtype=np.uint64)]
+    probes = [p for p in probes if p not in inside]
+    assert np.all(S.index(np.array(probes, dtype=np.uint64)) == -1)

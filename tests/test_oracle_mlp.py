@@ -80,3 +80,28 @@ def test_bf16_emulation_changes_results_only_at_bf16_scale():
     _, gq = mlp.loss_and_grad(p, x, T, IN, HID, OUT, bf16=True)
     d = np.abs(g - gq).max() / np.abs(g).max()
     assert 1e-5 < d < 3e-2
+
+
+def test_adam_recurrence_over_many_steps():
+    """Adam's moments carried across steps.  With a constant gradient g the
+    moments are m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so every
+    bias-corrected step is -lr g / (|g| + eps); with a gradient that flips sign
+    every step, m_t = (1 - b1) g (-1)^(t-1) (1 - (-b1)^t) / (1 + b1)
+    (a geometric series) while v_t keeps the constant-gradient value."""
+    b1, b2, lr, eps = 0.9, 0.999, 0.01, 1e-8
+    g = np.array([2.0, -0.5, 1e-3, 7.0])
+    w, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    T = 25
+    for t in range(1, T + 1):
+        w, m, v = mlp.adam(w, g, m, v, lr=lr, t=t, b1=b1, b2=b2, eps=eps)
+        assert np.allclose(m, (1 - b1 ** t) * g, rtol=1e-13, atol=0)
+        assert np.allclose(v, (1 - b2 ** t) * g * g, rtol=1e-12, atol=0)
+    assert np.allclose(w, -T * lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+    m, v = np.zeros(4), np.zeros(4)
+    w = np.zeros(4)
+    for t in range(1, T + 1):
+        gt = g * (-1) ** (t - 1)
+        w, m, v = mlp.adam(w, gt, m, v, lr=lr, t=t, b1=b1, b2=b2, eps=eps)
+        m_closed = (1 - b1) * g * (-1) ** (t - 1) * (1 - (-b1) ** t) / (1 + b1)
+        assert np.allclose(m, m_closed, rtol=1e-12, atol=0)
+        assert np.allclose(v, (1 - b2 ** t) * g * g, rtol=1e-12, atol=0)
