@@ -249,6 +249,7 @@ def run_ours(args, rank, world, local_rank):
     H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
     S = ps.Sector.molecular(12, 6, 6)
     ps.prepare(H, S)
+    install_launch(ps, H, S, tdt, args.launch)
     x_can, _, _ = H.export()
     U = count_updates(x_can, 12, 12, 6, 6)
     psi_np = w.random_state(S.dim, w.MOL24.psi_seed)
@@ -410,6 +411,16 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def install_launch(ps, H, S, tdt, spec: str):
+    """--launch cols_per_thread,staged_rows,row_split,direct,ranked: install that
+    shape (pauli_set_launch_config) instead of the heuristic one."""
+    if not spec:
+        return
+    t, nb, sp, d, r = (int(v) for v in spec.split(","))
+    ps.set_launch_config(H, S, tdt, ps.LaunchConfig(cols_per_thread=t, staged_rows=nb, row_split=sp, direct=d,
+                                                    ranked=r, ms=0.0))
+
+
 def run_xxz(args, rank, world, local_rank):
     """30-site open XXZ chain (seed 1), Neel start: one H|psi> timing and Krylov
     real-time steps (m = 20, dt = 0.05, the step replayed as a CUDA graph), in the
@@ -430,6 +441,7 @@ def run_xxz(args, rank, world, local_rank):
         S = ps.Sector(n, ps.BLOCKS, nl, [(k, n // 2 - k) for k in range(0, min(nl, n // 2) + 1) if n // 2 - k <= n - nl])
         label = f"xxz{n} Sz=0 blocks, split {nl}|{n - nl}, D={S.dim}"
     ps.prepare(H, S)
+    install_launch(ps, H, S, torch.complex64, args.launch)
     xc, _, _ = H.export()
     # term updates of one apply in the full space = M * 2^n; in a sector count per term
     if S.kind == ps.FULL:
@@ -597,6 +609,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rotate", action="store_true", help="skip the 32-qubit rotation side measurement")
+    ap.add_argument("--launch", default="", help="cols_per_thread,staged_rows,row_split,direct,ranked of the apply")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

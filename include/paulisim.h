@@ -207,8 +207,14 @@ int pauli_expect(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype
  *   - a sector whose launch needs more than 65,536 blocks gets
  *     PAULI_EUNSUPPORTED (the 24-qubit (6a,6b) sector needs 924);
  *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture;
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     life of the process (a cudaDeviceReset in between is not supported);
+ *     make that first call before any stream capture;
+ *   - a full-space sector of a lattice operator that is applied in passes over
+ *     local bit sets (pauli_set_launch_config direct = 2, the default from 21
+ *     qubits) accumulates H psi in a vector: there hpsi_out must be given,
+ *     unless an earlier pauli_expect without it has already made the
+ *     operator's own scratch vector; otherwise PAULI_EUNSUPPORTED;
  *   - every call uses the same array, and each block overwrites its own
  *     partials before they are read, so no state from an earlier call
  *     matters; calls that overlap on the GPU (different streams, no ordering
@@ -342,6 +348,23 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
 /* The shape pauli_apply currently uses for this sector and dtype (needs a plan). */
 int pauli_get_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, pauli_launch_config *cfg);
 
+/* Cache of tuned shapes in a text file (one line per (operator, sector,
+ * dtype): a tag, a key, the dtype and the five fields and ms of
+ * pauli_launch_config).  The key is the device name, the sector's shape
+ * (qubits, split, kind, blocks, dimension), the operator's term and group
+ * counts and a 64-bit FNV-1a hash of its canonical arrays, so an entry is only
+ * installed on the operator and sector it was measured for.
+ * pauli_tune_save writes the shapes tuned or installed for (H, s) -- both
+ * dtypes, where present -- replacing earlier lines with the same key and
+ * dtype (the file is rewritten through a temporary file and a rename; writers
+ * of one file must not run concurrently).  pauli_tune_load installs every
+ * matching entry with pauli_set_launch_config and sets *found to their
+ * number (0 if the file does not exist).  Both need a plan (pauli_prepare)
+ * and are blocking.  Errors: PAULI_EINVAL for bad handles, a NULL path or an
+ * unwritable file. */
+int pauli_tune_save(pauli_sum *H, const pauli_sector *s, const char *path);
+int pauli_tune_load(pauli_sum *H, const pauli_sector *s, const char *path, int *found);
+
 /* ------------------------------------------------------------------------- */
 /* many independent states in one persistent launch                           */
 /* ------------------------------------------------------------------------- */
@@ -369,6 +392,14 @@ int pauli_batch_apply(pauli_batch *b, const void *const *psi_in, void *const *ps
  * the given vectors and keeps the fastest.  Blocking. */
 int pauli_batch_tune(pauli_batch *b, const void *const *psi_in, void *const *psi_out, int reps,
                      pauli_launch_config *best, pauli_stream_t st);
+
+/* Installs a launch shape for the batch (cols_per_thread 1, 2 or 4,
+ * staged_rows 1 or 2, ranked 0 or 1; row_split must be 1 and direct 0):
+ * PAULI_EUNSUPPORTED if the staging layout does not fit in shared memory for
+ * the widest state.  pauli_batch_get_launch_config reads the shape in use
+ * (ms = 0). */
+int pauli_batch_set_launch_config(pauli_batch *b, const pauli_launch_config *cfg);
+int pauli_batch_get_launch_config(const pauli_batch *b, pauli_launch_config *cfg);
 
 int pauli_batch_destroy(pauli_batch *b);
 

@@ -74,9 +74,13 @@ SIGNATURES = {
     "pauli_tune": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp]),
     "pauli_set_launch_config": (_i32, [_vp, _vp, _i32, _vp]),
     "pauli_get_launch_config": (_i32, [_vp, _vp, _i32, _vp]),
+    "pauli_tune_save": (_i32, [_vp, _vp, C.c_char_p]),
+    "pauli_tune_load": (_i32, [_vp, _vp, C.c_char_p, _vp]),
     "pauli_batch_create": (_i32, [_i32, _vp, _vp, _i32, _vp]),
     "pauli_batch_apply": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "pauli_batch_tune": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "pauli_batch_set_launch_config": (_i32, [_vp, _vp]),
+    "pauli_batch_get_launch_config": (_i32, [_vp, _vp]),
     "pauli_batch_destroy": (_i32, [_vp]),
     "pauli_krylov_create": (_i32, [_vp, _vp, _i32, _i32, _vp]),
     "pauli_krylov_step": (_i32, [_vp, _vp, _dbl, _i32, _i32, _vp]),
@@ -363,41 +367,25 @@ class LaunchConfig(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-def _tune_key(H: PauliSum, s: Sector, code: int) -> str:
-    import hashlib
-    import torch
-    n, m, g = H.info()
-    x, z, c = H.export()
-    fp = hashlib.sha256(x.tobytes() + z.tobytes() + c.tobytes()).hexdigest()[:16]
-    return (f"{torch.cuda.get_device_name()}|n{n}|lo{s.n_lo}|k{s.kind}|b{s.blocks}|d{s.dim}|M{m}|G{g}|"
-            f"{'c64' if code == C64 else 'c128'}|{fp}")
-
-
 def tune(H: PauliSum, s: Sector, dtype=None, reps: int = 5, cache: str | None = None, stream=None) -> dict:
     """Pick the fastest launch shape for (H, s, dtype) by timing the candidates
-    (pauli_tune), or install it from a JSON cache of earlier results."""
-    import json
+    (pauli_tune), or install it from a cache file of earlier results
+    (pauli_tune_load / pauli_tune_save)."""
     import torch
     code = C64 if dtype in (None, torch.complex64) else C128
-    key = _tune_key(H, s, code)
-    db = {}
-    if cache and os.path.exists(cache):
-        with open(cache) as f:
-            db = json.load(f)
-    if key in db:
-        cfg = LaunchConfig(**db[key])
-        _check(lib().pauli_set_launch_config(H._h, s._h, code, C.byref(cfg)))
-        return dict(db[key], cached=True)
+    if cache:
+        prepare(H, s)
+        found = C.c_int(0)
+        _check(lib().pauli_tune_load(H._h, s._h, os.fsencode(cache), C.byref(found)))
+        if found.value:
+            out = launch_config(H, s, torch.complex64 if code == C64 else torch.complex128)
+            if out["ms"] > 0:
+                return dict(out, cached=True)
     cfg = LaunchConfig()
     _check(lib().pauli_tune(H._h, s._h, code, reps, C.byref(cfg), _stream_ptr(stream)))
-    out = cfg.as_dict()
     if cache:
-        db[key] = out
-        tmp = cache + f".{os.getpid()}.tmp"
-        with open(tmp, "w") as f:
-            json.dump(db, f, indent=1, sort_keys=True)
-        os.replace(tmp, cache)
-    return dict(out, cached=False)
+        _check(lib().pauli_tune_save(H._h, s._h, os.fsencode(cache)))
+    return dict(cfg.as_dict(), cached=False)
 
 
 def set_launch_config(H: PauliSum, s: Sector, dtype, cfg: "LaunchConfig"):
@@ -457,6 +445,14 @@ class Batch:
         cfg = LaunchConfig()
         _check(lib().pauli_batch_tune(self._h, self._ptrs(psis, "psi_in"), self._ptrs(outs, "psi_out", True), reps,
                                       C.byref(cfg), _stream_ptr(stream)))
+        return cfg.as_dict()
+
+    def set_launch_config(self, cfg: "LaunchConfig"):
+        _check(lib().pauli_batch_set_launch_config(self._h, C.byref(cfg)))
+
+    def launch_config(self) -> dict:
+        cfg = LaunchConfig()
+        _check(lib().pauli_batch_get_launch_config(self._h, C.byref(cfg)))
         return cfg.as_dict()
 
     def close(self):

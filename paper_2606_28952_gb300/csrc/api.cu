@@ -6,8 +6,10 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <utility>
 
 #include "ps_internal.cuh"
 
@@ -54,6 +56,34 @@ void dev_free(const Allocator &a, void *p) {
 }
 
 void init_sector_view(SectorView &v, int n, int kind, int n_lo, int nb, const int *klo, const int *khi);
+
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<int, const void *>, size_t> g_attr;  // (device, kernel) -> dynamic smem opted in
+constexpr int kMaxDev = 64;
+int g_sms[kMaxDev] = {};
+}  // namespace
+
+void smem_optin(const void *func, size_t bytes) {
+    if (bytes <= 48 * 1024) return;
+    int dev = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    size_t &have = g_attr[std::make_pair(dev, func)];
+    if (have >= bytes) return;
+    PS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have = bytes;
+}
+
+int num_sms() {
+    int dev = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < kMaxDev && g_sms[dev] > 0) return g_sms[dev];
+    int sms = 0;
+    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dev >= 0 && dev < kMaxDev) g_sms[dev] = sms;
+    return sms;
+}
 
 }  // namespace ps
 

@@ -343,16 +343,6 @@ k_rotate_pairs(int64_t npairs, int64_t nlo, const uint32_t *__restrict__ tab, in
 // 227 KB of shared memory per block on sm_103a, less room for the kernel's static arrays
 constexpr size_t kMaxDynSmem = 226 * 1024;
 
-int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        PS_CUDA(cudaGetDevice(&dev));
-        PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    }
-    return sms;
-}
-
 const LaunchChoice *find_tuned(const Plan &p, const SectorView &v, int dtype) {
     for (const TunedEntry &t : p.tuned)
         if (t.dim == v.dim && t.nblk == v.nblk && t.dtype == dtype) return &t.choice;
@@ -361,7 +351,7 @@ const LaunchChoice *find_tuned(const Plan &p, const SectorView &v, int dtype) {
 
 // Launch shape of one apply.  Each field is resolved from, in order: the
 // forced choice (the autotuner's candidate), the plan's tuned entry for this
-// sector and dtype, the PAULISIM_* environment overrides, the heuristics.
+// sector and dtype (pauli_set_launch_config / pauli_tune), the heuristics.
 ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split, const LaunchChoice *force) {
     ApplyCfg c;
     LaunchChoice ch;
@@ -377,7 +367,7 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     const bool single = v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1;
     const size_t bb_pattern = buf_bytes(1 << v.n_lo);
     const bool rank_ok = single && v.n_lo <= 16;
-    const int dflt_ranked = env_int("PAULISIM_RANKED", (single && bb_pattern > kMaxDynSmem) ? 1 : 0);
+    const int dflt_ranked = (single && bb_pattern > kMaxDynSmem) ? 1 : 0;
     c.ranked = rank_ok && (ch.ranked >= 0 ? ch.ranked != 0 : dflt_ranked != 0);
     const size_t bb = c.ranked ? buf_bytes(ranked_rowcap(v.dlo[0])) : bb_pattern;
     const size_t extra = c.ranked ? rank_table_bytes(v.n_lo) : 0;
@@ -386,12 +376,12 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     // rank-staged rows wider than ~100 KB leave one or two CTAs per SM: 8 columns per
     // thread then give each thread more independent gathers to overlap
     const bool wide_ranked = c.ranked && bb + extra > 100 * 1024 && mx >= 6 * kThreads;
-    int tpt = ch.tpt ? ch.tpt
-                     : env_int("PAULISIM_TPT", wide_ranked ? 8 : mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1));
+    int tpt = ch.tpt ? ch.tpt : (wide_ranked ? 8 : mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1));
     if (tpt == 8 && !c.ranked) tpt = 4;
     if (tpt != 1 && tpt != 2 && tpt != 4 && tpt != 8) tpt = 1;
-    int nbuf = ch.nbuf ? ch.nbuf : env_int("PAULISIM_NBUF", 1);
+    int nbuf = ch.nbuf ? ch.nbuf : 1;
     if (nbuf != 1 && nbuf != 2) nbuf = 1;
+    if (tpt == 8) nbuf = 1;  // 8 columns per thread exist for one staged row only
     if (nbuf * bb + extra > kMaxDynSmem) nbuf = 1;
     c.tpt = tpt;
     c.nbuf = nbuf;
@@ -400,7 +390,7 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     // full space with a local-pass plan (lattice operators, 2^21 amplitudes or more):
     // chunks staged in shared memory, one pass per local bit set
     if (v.kind == PAULI_SECTOR_FULL && p.local) {
-        const int dflt_local = env_int("PAULISIM_LOCAL", v.n >= 21 ? 1 : 0);
+        const int dflt_local = v.n >= 21 ? 1 : 0;
         if (ch.direct >= 0 ? ch.direct == 2 : dflt_local != 0) {
             c.local = true;
             c.direct = false;
@@ -420,7 +410,7 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     const ListTab *lt = single ? find_lists(p, v.klo[0]) : nullptr;
     bool use_list = false;
     if (lt) {
-        const int dflt_list = env_int("PAULISIM_LIST", (dtype == PAULI_C128 && v.dlo[0] >= 384) ? 1 : 0);
+        const int dflt_list = (dtype == PAULI_C128 && v.dlo[0] >= 384) ? 1 : 0;
         use_list = ch.direct >= 0 ? ch.direct == 3 : dflt_list != 0;
     }
     if (use_list) {
@@ -435,9 +425,13 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     // small operators (lattice models): the whole folded plan fits in shared
     // memory and rows have few pieces, so gather straight from global memory
     const bool fits = p.I <= kDirectItems && p.S <= kDirectSegs;
-    const int dflt_direct = env_int("PAULISIM_DIRECT", fits ? 1 : 0);
+    const int dflt_direct = fits ? 1 : 0;
     c.direct = !use_list && fits && (ch.direct >= 0 ? ch.direct == 1 : dflt_direct != 0);
     if (c.direct) {
+        // the direct gather stages nothing and has 1, 2 or 4 columns per thread
+        c.ranked = false;
+        if (c.tpt == 8) c.tpt = 4;
+        c.base_nct = make_geom(v, c.tpt * kThreads).cta_off[v.nblk];
         c.smem = 0;
         c.nbuf = 1;
         c.nsplit = 1;
@@ -457,7 +451,7 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
         const int per_sm = std::max<int>(1, std::min<int>(2048 / kThreads, (int)((228 * 1024) / (c.smem + 2048))));
         const int64_t slots = (int64_t)num_sms() * per_sm;
         if (c.base_nct < 16 * slots) nsplit = (int)((16 * slots + c.base_nct - 1) / c.base_nct);
-        nsplit = ch.nsplit ? ch.nsplit : env_int("PAULISIM_SPLIT", nsplit);
+        if (ch.nsplit) nsplit = ch.nsplit;
         nsplit = std::max(1, std::min<int>({nsplit, kMaxSplit, (int)std::max<int64_t>(1, p.P / 8)}));
     }
     c.nsplit = nsplit;

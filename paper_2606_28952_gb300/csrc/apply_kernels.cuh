@@ -1110,12 +1110,6 @@ k_combine(int nsplit, int64_t dim, const typename Cx<R>::T *__restrict__ part, c
     }
 }
 
-int env_int(const char *name, int dflt) {
-    const char *e = std::getenv(name);
-    if (!e || !*e) return dflt;
-    return std::atoi(e);
-}
-
 Geom make_geom(const SectorView &v, int tile, int nsplit = 1, const int32_t *split_p0 = nullptr,
                int32_t npieces = 0) {
     Geom g;
@@ -1166,11 +1160,7 @@ void launch_one(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, const
                 void *out, double *partials, int flags, cudaStream_t st) {
     using C2 = typename Cx<R>::T;
     auto run = [&](auto kern) {
-        static size_t attr_bytes = 48 * 1024;  // dynamic shared memory this kernel is opted in for
-        if (cfg.smem > attr_bytes) {
-            PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
-            attr_bytes = cfg.smem;
-        }
+        smem_optin(reinterpret_cast<const void *>(kern), cfg.smem);
         kern<<<(unsigned)cfg.nct, kThreads, cfg.smem, st>>>(v, geo, pd, static_cast<const C2 *>(in),
                                                              static_cast<C2 *>(out), partials, flags);
         PS_LAUNCH_CHECK();

@@ -35,19 +35,13 @@ struct pauli_batch {
 namespace ps_batch {
 constexpr uint32_t kBatchMagic = 0x50424131u;
 
-int env_int2(const char *name, int dflt) {
-    const char *e = std::getenv(name);
-    return (e && *e) ? std::atoi(e) : dflt;
-}
-
 template <typename R, int KIND, bool REALH, int TPT, int NBUF>
 void launch_batch_t(pauli_batch *b, size_t smem, double *results, bool want_out, cudaStream_t st) {
     auto kern = k_apply_batch<R, KIND, REALH, TPT, NBUF>;
-    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0, dev = 0, sms = 0;
+    smem_optin(reinterpret_cast<const void *>(kern), smem);
+    int per_sm = 0;
     PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    PS_CUDA(cudaGetDevice(&dev));
-    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int sms = num_sms();
     PS_CHECK(per_sm >= 1, PAULI_EUNSUPPORTED, "batched apply: the launch shape does not fit on an SM");
     const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, std::max<int64_t>(1, b->total));
     PS_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st));
@@ -190,7 +184,7 @@ int pauli_batch_create(int n, pauli_sum *const *H, const pauli_sector *const *S,
             b->h_ptrs.resize(n);
             int64_t mx = 0;
             for (int i = 0; i < n; ++i) mx = std::max<int64_t>(mx, S[i]->v.dlo[0]);
-            const int tpt = env_int2("PAULISIM_TPT", mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1));
+            const int tpt = mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1);
             build_descs(b, (tpt == 1 || tpt == 2 || tpt == 4) ? tpt : 1);
             b->nbuf = 1;
             b->ranked = batch_smem(b, 1, false) > 226 * 1024;
@@ -311,6 +305,47 @@ int pauli_batch_tune(pauli_batch *b, const void *const *psi_in, void *const *psi
         set_error("unexpected internal error");
         return PAULI_EINVAL;
     }
+}
+
+int pauli_batch_set_launch_config(pauli_batch *b, const pauli_launch_config *cfg) {
+    try {
+        clear_error();
+        PS_CHECK(b && b->magic == kBatchMagic, PAULI_EINVAL, "not a valid pauli_batch handle");
+        PS_CHECK(cfg != nullptr, PAULI_EINVAL, "cfg is NULL");
+        PS_CHECK(cfg->cols_per_thread == 1 || cfg->cols_per_thread == 2 || cfg->cols_per_thread == 4, PAULI_EINVAL,
+                 "batch: cols_per_thread must be 1, 2 or 4");
+        PS_CHECK(cfg->staged_rows == 1 || cfg->staged_rows == 2, PAULI_EINVAL, "staged_rows must be 1 or 2");
+        PS_CHECK(cfg->ranked == 0 || cfg->ranked == 1, PAULI_EINVAL, "ranked must be 0 or 1");
+        PS_CHECK(cfg->row_split == 1 && cfg->direct == 0, PAULI_EUNSUPPORTED,
+                 "batch: only the staged gather without row splits runs in the batched launch");
+        PS_CHECK(batch_smem(b, cfg->staged_rows, cfg->ranked != 0) <= 226 * 1024, PAULI_EUNSUPPORTED,
+                 "batch: this staging layout does not fit in shared memory for the widest state");
+        build_descs(b, cfg->cols_per_thread);
+        b->nbuf = cfg->staged_rows;
+        b->ranked = cfg->ranked != 0;
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PAULI_EINVAL;
+    }
+}
+
+int pauli_batch_get_launch_config(const pauli_batch *b, pauli_launch_config *cfg) {
+    if (!b || b->magic != kBatchMagic || !cfg) {
+        set_error("invalid pauli_batch handle or NULL cfg");
+        return PAULI_EINVAL;
+    }
+    clear_error();
+    cfg->cols_per_thread = b->tpt;
+    cfg->staged_rows = b->nbuf;
+    cfg->row_split = 1;
+    cfg->direct = 0;
+    cfg->ranked = b->ranked ? 1 : 0;
+    cfg->ms = 0.0;
+    return PAULI_OK;
 }
 
 int pauli_batch_destroy(pauli_batch *b) {

@@ -242,7 +242,7 @@ void launch_list_k(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, co
                    const void *in, void *out, double *partials, int flags, cudaStream_t st) {
     using C2 = typename Cx<R>::T;
     auto kern = k_apply_list<R, REALH>;
-    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
+    smem_optin(reinterpret_cast<const void *>(kern), cfg.smem);
     kern<<<(unsigned)cfg.nct, kListThreads, cfg.smem, st>>>(v, geo, pd, ld, static_cast<const C2 *>(in),
                                                          static_cast<C2 *>(out), partials, flags);
     PS_LAUNCH_CHECK();

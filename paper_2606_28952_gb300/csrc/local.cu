@@ -474,6 +474,7 @@ LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st) {
 }
 
 int64_t local_last_chunks(const LocalPlan *lp) { return lp ? lp->pass[lp->npass - 1].nchunk : 0; }
+int64_t local_scratch_bytes(const LocalPlan *lp) { return lp ? lp->scratch_bytes : 0; }
 int local_passes(const LocalPlan *lp) { return lp ? lp->npass : 0; }
 
 size_t local_smem(const LocalPlan *lp, int p, int dtype) {
@@ -509,10 +510,7 @@ static void launch_local_r(LocalPlan *lp, const void *in, void *out, double *par
         const bool last = p + 1 == lp->npass;
         const int flags = (p == 0 ? 1 : 8) | ((last && partials) ? 2 : 0);
         auto run = [&](auto kern) {
-            // per launch: the real and complex kernels share this lambda's type, so a
-            // cached "already raised" size would be wrong for one of them
-            if (smem > 48 * 1024)
-                PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            smem_optin(reinterpret_cast<const void *>(kern), smem);
             kern<<<(unsigned)Q.nchunk, kThreads, smem, st>>>(P, A, static_cast<const C2 *>(in),
                                                               static_cast<C2 *>(out), partials, flags);
             PS_LAUNCH_CHECK();

@@ -51,6 +51,13 @@ void set_current_allocator(const Allocator &a);
 void *dev_alloc(const Allocator &a, size_t bytes);
 void dev_free(const Allocator &a, void *p);
 
+// Opts kernel `func` in to `bytes` of dynamic shared memory on the current
+// device.  The attribute is per device, so the set of (device, kernel) pairs
+// already raised to at least `bytes` is remembered per device (api.cu).
+void smem_optin(const void *func, size_t bytes);
+// SM count of the current device (cached per device ordinal).
+int num_sms();
+
 // RAII device buffer (library-internal temporaries at build time).
 template <typename T>
 struct DevBuf {
@@ -268,14 +275,8 @@ void jw_fermion_raw_device(int n, int nterms, const int *nf, const int *modes, c
                            int64_t &count, cudaStream_t st);
 // Plans are keyed by (n_lo, merged): a single-block sector uses a plan whose
 // segments merge the low Z masks z_lo and z_lo ^ x_lo (exact on every pair the
-// sector keeps; PAULISIM_MERGE=0 turns it off), other sectors the plain plan.
-inline bool plan_merges(const SectorView &v) {
-    static const int on = [] {
-        const char *e = getenv("PAULISIM_MERGE");
-        return e ? atoi(e) : 1;
-    }();
-    return on != 0 && v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1;
-}
+// sector keeps), other sectors the plain plan.
+inline bool plan_merges(const SectorView &v) { return v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1; }
 Plan &get_plan(pauli_sum *h, const SectorView &v, cudaStream_t st);
 Plan *find_plan(pauli_sum *h, const SectorView &v);  // existing plan or nullptr; never builds
 void free_plan(const Allocator &al, Plan &p);
@@ -339,6 +340,8 @@ void launch_list(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const 
 LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st);
 void free_local_plan(LocalPlan *lp);
 int64_t local_last_chunks(const LocalPlan *lp);
+// bytes of the plan's H psi scratch (used when the caller passes no output vector)
+int64_t local_scratch_bytes(const LocalPlan *lp);
 int local_passes(const LocalPlan *lp);
 void launch_local(LocalPlan *lp, const void *in, void *out, int dtype, int64_t dim, double *partials, cudaStream_t st);
 

@@ -4,7 +4,11 @@
 // the fastest is kept in the operator's plan for that sector.
 #include <algorithm>
 #include <cfloat>
+#include <cstdio>
 #include <cstdlib>
+#include <fstream>
+#include <sstream>
+#include <string>
 #include <vector>
 
 #include "ps_internal.cuh"
@@ -13,10 +17,7 @@ using namespace ps;
 
 namespace {
 
-int env_or(const char *name, int dflt) {
-    const char *e = std::getenv(name);
-    return (e && *e) ? std::atoi(e) : dflt;
-}
+constexpr int kTuneMaxCandidates = 96;
 
 void store_tuned(Plan &p, const SectorView &v, int dtype, const LaunchChoice &c, double ms) {
     for (TunedEntry &t : p.tuned)
@@ -48,6 +49,50 @@ pauli_launch_config to_public(const ApplyCfg &c, double ms) {
     o.ms = ms;
     return o;
 }
+
+
+// Cache key of (H, s) on the current device: the device name, the sector's
+// shape, the operator's sizes and a 64-bit FNV-1a fingerprint of its canonical
+// arrays (x, z, C), so that a cached shape is only installed on the operator and
+// sector it was measured for.
+std::string tune_key(const pauli_sum *H, const pauli_sector *s) {
+    int dev = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    PS_CUDA(cudaGetDeviceProperties(&prop, dev));
+    std::string name(prop.name);
+    for (char &ch : name)
+        if (ch == ' ' || ch == '|' || ch == '\t') ch = '_';
+    uint64_t fp = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t bytes) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < bytes; ++i) {
+            fp ^= b[i];
+            fp *= 1099511628211ull;
+        }
+    };
+    if (H->m > 0) {
+        std::vector<uint64_t> hx(H->m), hz(H->m);
+        std::vector<double2> hc(H->m);
+        PS_CUDA(cudaMemcpy(hx.data(), H->x, H->m * 8, cudaMemcpyDeviceToHost));
+        PS_CUDA(cudaMemcpy(hz.data(), H->z, H->m * 8, cudaMemcpyDeviceToHost));
+        PS_CUDA(cudaMemcpy(hc.data(), H->c, H->m * 16, cudaMemcpyDeviceToHost));
+        mix(hx.data(), hx.size() * 8);
+        mix(hz.data(), hz.size() * 8);
+        mix(hc.data(), hc.size() * 16);
+    }
+    const SectorView &v = s->v;
+    std::ostringstream k;
+    k << name << "|n" << v.n << "|lo" << v.n_lo << "|k" << v.kind << "|b";
+    if (v.kind == PAULI_SECTOR_BLOCKS)
+        for (int b = 0; b < v.nblk; ++b) k << (b ? "," : "") << v.klo[b] << ":" << v.khi[b];
+    char hex[17];
+    std::snprintf(hex, sizeof(hex), "%016llx", (unsigned long long)fp);
+    k << "|d" << v.dim << "|M" << H->m << "|G" << H->G << "|" << hex;
+    return k.str();
+}
+
+constexpr const char *kTuneTag = "paulisim-tune-v1";
 
 }  // namespace
 
@@ -110,8 +155,8 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
                         cand.push_back(c);
                     }
         }
-        const int limit = env_or("PAULISIM_TUNE_MAX", 96);
-        if ((int)cand.size() > limit) cand.resize(limit);
+        // at most kTuneMaxCandidates shapes are timed (in the order enumerated above)
+        if ((int)cand.size() > kTuneMaxCandidates) cand.resize(kTuneMaxCandidates);
         // scratch states and the largest split buffer any candidate needs
         const size_t es = dtype == PAULI_C64 ? 8 : 16;
         int64_t need = 0;
@@ -223,6 +268,101 @@ int pauli_get_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, paul
     } catch (const Error &e) {
         set_error(e.msg);
         return e.code;
+    }
+}
+
+int pauli_tune_save(pauli_sum *H, const pauli_sector *s, const char *path) {
+    try {
+        clear_error();
+        PS_CHECK(H && H->magic == kSumMagic, PAULI_EINVAL, "not a valid pauli_sum handle");
+        PS_CHECK(s && s->magic == kSectorMagic, PAULI_EINVAL, "not a valid pauli_sector handle");
+        PS_CHECK(path != nullptr && *path, PAULI_EINVAL, "path is NULL or empty");
+        Plan *p = find_plan(H, s->v);
+        PS_CHECK(p != nullptr, PAULI_EINVAL, "no plan for this sector split yet: call pauli_prepare first");
+        const std::string key = tune_key(H, s);
+        std::vector<std::string> keep;
+        {
+            std::ifstream in(path);
+            std::string line;
+            while (std::getline(in, line)) {
+                std::istringstream ls(line);
+                std::string tag, k, dt;
+                if (!(ls >> tag >> k >> dt) || tag != kTuneTag) continue;
+                bool replaced = false;
+                for (const TunedEntry &t : p->tuned)
+                    if (t.dim == s->v.dim && t.nblk == s->v.nblk && k == key &&
+                        dt == (t.dtype == PAULI_C64 ? "c64" : "c128"))
+                        replaced = true;
+                if (!replaced) keep.push_back(line);
+            }
+        }
+        int wrote = 0;
+        for (const TunedEntry &t : p->tuned) {
+            if (t.dim != s->v.dim || t.nblk != s->v.nblk) continue;
+            std::ostringstream ls;
+            ls.precision(17);
+            ls << kTuneTag << " " << key << " " << (t.dtype == PAULI_C64 ? "c64" : "c128") << " " << t.choice.tpt << " "
+               << t.choice.nbuf << " " << t.choice.nsplit << " " << t.choice.direct << " " << t.choice.ranked << " "
+               << t.ms;
+            keep.push_back(ls.str());
+            ++wrote;
+        }
+        const std::string tmp = std::string(path) + ".tmp";
+        {
+            std::ofstream out(tmp, std::ios::trunc);
+            PS_CHECK(out.good(), PAULI_EINVAL, std::string("cannot write ") + tmp);
+            for (const std::string &l : keep) out << l << "\n";
+            out.flush();
+            PS_CHECK(out.good(), PAULI_EINVAL, std::string("write to ") + tmp + " failed");
+        }
+        PS_CHECK(std::rename(tmp.c_str(), path) == 0, PAULI_EINVAL, std::string("cannot replace ") + path);
+        (void)wrote;
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PAULI_EINVAL;
+    }
+}
+
+int pauli_tune_load(pauli_sum *H, const pauli_sector *s, const char *path, int *found) {
+    try {
+        clear_error();
+        PS_CHECK(H && H->magic == kSumMagic, PAULI_EINVAL, "not a valid pauli_sum handle");
+        PS_CHECK(s && s->magic == kSectorMagic, PAULI_EINVAL, "not a valid pauli_sector handle");
+        PS_CHECK(H->n == s->v.n, PAULI_EINVAL, "operator and sector have different qubit counts");
+        PS_CHECK(path != nullptr && *path, PAULI_EINVAL, "path is NULL or empty");
+        PS_CHECK(found != nullptr, PAULI_EINVAL, "found is NULL");
+        *found = 0;
+        std::ifstream in(path);
+        if (!in.good()) return PAULI_OK;  // no cache yet
+        const std::string key = tune_key(H, s);
+        std::string line;
+        std::vector<std::pair<int, pauli_launch_config>> hits;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string tag, k, dt;
+            pauli_launch_config c;
+            if (!(ls >> tag >> k >> dt >> c.cols_per_thread >> c.staged_rows >> c.row_split >> c.direct >> c.ranked >>
+                  c.ms))
+                continue;
+            if (tag != kTuneTag || k != key || (dt != "c64" && dt != "c128")) continue;
+            hits.emplace_back(dt == "c64" ? PAULI_C64 : PAULI_C128, c);
+        }
+        for (const auto &h : hits) {
+            const int rc = pauli_set_launch_config(H, s, h.first, &h.second);
+            if (rc != PAULI_OK) return rc;
+            ++*found;
+        }
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PAULI_EINVAL;
     }
 }
 

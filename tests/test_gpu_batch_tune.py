@@ -84,6 +84,10 @@ def test_tune_single_and_cache(ps, tmp_path):
     cache = str(tmp_path / "tune.json")
     cfg = ps.tune(H, S, torch.complex64, reps=2, cache=cache)
     assert not cfg["cached"] and cfg["ms"] > 0
+    # the cache is the C library's text file (pauli_tune_save)
+    lines = [ln.split() for ln in open(cache).read().splitlines()]
+    assert len(lines) == 1 and lines[0][0] == "paulisim-tune-v1" and lines[0][2] == "c64"
+    assert int(lines[0][3]) == cfg["cols_per_thread"]
     assert ps.launch_config(H, S, torch.complex64)["cols_per_thread"] == cfg["cols_per_thread"]
     psi = w.random_state(S.dim, 3)
     x = torch.from_numpy(psi).to("cuda", torch.complex64)
