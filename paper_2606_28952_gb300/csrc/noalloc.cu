@@ -30,7 +30,9 @@ std::mutex g_mu;
 double *g_addr[kMaxDevices] = {};
 
 // Device address of g_expect_scratch on the current device (set-up on the
-// first call for each device, with that device current).
+// first call for each device, with that device current).  The address is kept
+// for the life of the process: it assumes that no cudaDeviceReset runs in
+// between (a reset reloads the module and may move the array).
 double *scratch_on_current_device() {
     int dev = 0;
     PS_CUDA(cudaGetDevice(&dev));
@@ -70,6 +72,14 @@ extern "C" int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const v
         Plan *p = find_plan(H, s->v);
         PS_CHECK(p != nullptr, PAULI_EINVAL,
                  "no apply plan for this sector split: call pauli_prepare(H, s) once before pauli_expect_noalloc");
+        // the full-space pass kernel accumulates H psi across its passes: without an
+        // output vector it would use (and on first use allocate) the plan's own
+        // dim-sized scratch, so that case needs hpsi_out or an existing scratch
+        const ApplyCfg cfg = apply_config(*p, s->v, dtype, false);
+        if (cfg.local && !hpsi_out)
+            PS_CHECK(local_scratch_bytes(p->local) >= (int64_t)bytes, PAULI_EUNSUPPORTED,
+                     "pauli_expect_noalloc: this full-space operator is applied in passes that accumulate H psi in "
+                     "a vector; pass hpsi_out (a dim-sized vector) or call pauli_expect once without it first");
         // one CTA per (row, column tile), no split: the launch touches no scratch but the static array
         const int64_t nct = apply_num_ctas(*p, s->v, dtype, false);
         PS_CHECK(nct <= kNoallocMaxBlocks, PAULI_EUNSUPPORTED,

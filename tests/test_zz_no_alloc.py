@@ -91,3 +91,56 @@ def test_noalloc_rejections(ps):
                                        C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == ps.EUNSUPPORTED
     assert "static scratch" in ps.lib().pauli_last_error().decode()
+
+
+def test_noalloc_full_space_passes(ps):
+    """A 22-site chain in the full space runs in passes over local bit sets,
+    which accumulate H psi in a vector.  Without hpsi_out the call is refused
+    (the passes would need a vector the library would have to allocate) until
+    an ordinary pauli_expect has made the operator's own one; with hpsi_out, or
+    after that, it matches pauli_expect, and free device memory does not move
+    across the no-allocation calls."""
+    import torch
+    n = 22
+    x, z, cre, cim = w.xxz_terms(n, 1)
+    H = ps.PauliSum.from_terms(n, x, z, cre, cim)
+    S = ps.Sector.full(n)
+    ps.prepare(H, S)
+    assert ps.launch_config(H, S)["direct"] == 2
+    psi = torch.from_numpy(w.random_state(S.dim, 22)).to("cuda", torch.complex64)
+    res = torch.empty(4, dtype=torch.float64, device="cuda")
+    hp = torch.empty_like(psi)
+    assert _noalloc(ps, H, S, psi, res) == ps.EUNSUPPORTED
+    assert "hpsi_out" in ps.lib().pauli_last_error().decode()
+    # the first successful call on a device looks up the static array (which may
+    # load the library's module onto the device); memory is compared after it
+    rc = _noalloc(ps, H, S, psi, res, hp)
+    assert rc == 0, ps.lib().pauli_last_error()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        rc = _noalloc(ps, H, S, psi, res, hp)
+        assert rc == 0, ps.lib().pauli_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    got = res.cpu().numpy()
+    ref_h = torch.empty_like(psi)
+    ref = ps.expect(H, S, psi, hpsi_out=ref_h).cpu().numpy()
+    assert abs(complex(got[0], got[1]) - complex(ref[0], ref[1])) <= 1e-6 * max(1.0, abs(ref[0]))
+    assert abs(got[2] - ref[2]) <= 1e-5 * ref[2]
+    a = hp.cpu().numpy().astype(np.complex128)
+    b = ref_h.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+    # an ordinary expectation without an output vector makes the operator's scratch;
+    # from then on the no-allocation call works without hpsi_out too
+    ref2 = ps.expect(H, S, psi).cpu().numpy()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        res.fill_(float("nan"))
+        rc = _noalloc(ps, H, S, psi, res)
+        assert rc == 0, ps.lib().pauli_last_error()
+        torch.cuda.synchronize()
+        got = res.cpu().numpy()
+        assert abs(complex(got[0], got[1]) - complex(ref2[0], ref2[1])) <= 1e-6 * max(1.0, abs(ref2[0]))
+    assert torch.cuda.mem_get_info()[0] == free1
