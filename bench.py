@@ -372,6 +372,18 @@ def run_ours(args, rank, world, local_rank):
         del phi
         torch.cuda.empty_cache()
 
+    # side measurements on the other workloads (same build, same run): the
+    # bandwidth-graded lattice applies, the persistent batch against sequential
+    # launches in both precisions, and the 32-qubit molecule
+    side_wl = {}
+    if not args.no_side:
+        side_wl["xxz30_full_apply_c64"] = xxz_apply_measure(ps, dev, w.XXZ_SITES, False, reps=10)
+        side_wl["xxz30_sz0_apply_c64"] = xxz_apply_measure(ps, dev, w.XXZ_SITES, True, reps=20)
+        side_wl["batched64_c64"] = batched_measure(
+            ps, dev, warmup=1, steps=3, seeded_states=False,
+            shape=ps.LaunchConfig(cols_per_thread=4, staged_rows=1, row_split=1, direct=0, ranked=1, ms=0.0))
+        side_wl["mol32_apply_c64"] = mol32_apply_measure(ps, dev, reps=2)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, nrows, dt, est = oracle_rate(seconds=args.ref_seconds)
@@ -390,6 +402,8 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"},
             "roofline": {"bound": "alu", "achieved": achieved_gups, "peak": popc_peak, "unit": "Gupd/s",
                          "frac": achieved_gups / popc_peak,
+                         "eff_hbm": achieved_gbs / hbm_peak, "eff_hbm_achieved_gbs": achieved_gbs,
+                         "eff_hbm_compulsory_bytes": alg_bytes, "eff_hbm_peak_gbs": hbm_peak,
                          "traffic": profiled_traffic("k_apply_mol24_c64.json") if args.dtype == "c64" else None,
                          "note": (f"updates U={U} per launch / CUDA-event step time (the step is the gather "
                                   f"kernel plus, when rows are split, its fixed-order combine: "
@@ -404,7 +418,10 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "side": {"expect_ms": t_expect * 1e3, f"apply_{'c128' if tdt == torch.complex64 else 'c64'}_ms": t_other * 1e3,
                      "step_times_ms_min_max": [min(times_ms), max(times_ms)],
-                     "launch_shape": lc, "rotate_pair_double_32q_c64": rot},
+                     "launch_shape": lc, "rotate_pair_double_32q_c64": rot,
+                     "fp32_vs_fp64_24q": {"c64_ms": t_step * 1e3 if tdt == torch.complex64 else t_other * 1e3,
+                                          "c128_ms": t_other * 1e3 if tdt == torch.complex64 else t_step * 1e3},
+                     **side_wl},
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -515,18 +532,16 @@ def run_xxz(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
-def run_batched(args, rank, world, local_rank):
+def batched_measure(ps, dev, warmup: int, steps: int, tune_reps: int = 2, shape=None, seeded_states=True):
     """64 independent synthetic molecules (n_orb ~ U{8..14}, half filling): one
-    persistent complex64 launch of H_b psi_b + <H>_b (FP64 reductions, launch
-    shape from the autotuner) vs 64 sequential complex128 pauli_expect calls."""
+    persistent complex64 launch of H_b psi_b + <H>_b (FP64 reductions) against 64
+    sequential complex128 and 64 sequential complex64 pauli_expect calls, all on
+    this build.  The launch shape comes from the autotuner (tune_reps > 0) or is
+    installed (shape = LaunchConfig)."""
     import torch
-    import paper_2606_28952_gb300 as ps
-
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
     mols = w.batched_states(64, 3)
     t0 = time.perf_counter()
-    Hs, Ss, U = [], [], 0
+    Hs, Ss, U, Bc = [], [], 0, 0
     for m in mols:
         h, g = m.integrals()
         H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
@@ -535,28 +550,41 @@ def run_batched(args, rank, world, local_rank):
         Ss.append(S)
         xc, _, _ = H.export()
         U += count_updates(xc, m.norb, m.norb, m.n_alpha, m.n_beta)
+        Bc += 2 * S.dim * 8 + H.m * 24 + H.n_groups * 16
     t_build = time.perf_counter() - t0
     dims = [S.dim for S in Ss]
-    psis = [torch.from_numpy(w.random_state(S.dim, m.psi_seed)).to(dev) for S, m in zip(Ss, mols)]  # c128
+    if seeded_states:
+        psis = [torch.from_numpy(w.random_state(S.dim, m.psi_seed)).to(dev) for S, m in zip(Ss, mols)]  # c128
+    else:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(2000)
+        psis = []
+        for S in Ss:
+            v = torch.randn(S.dim, dtype=torch.complex128, device=dev, generator=gen)
+            psis.append(v / torch.linalg.vector_norm(v))
     x64 = [p.to(torch.complex64) for p in psis]
     outs = [torch.empty_like(x) for x in x64]
     B = ps.Batch(Hs, Ss, dtype=torch.complex64)
-    cfg = B.tune(x64, outs, reps=2)
+    if shape is not None:
+        B.set_launch_config(shape)
+        cfg = dict(B.launch_config(), source="installed")
+    else:
+        cfg = dict(B.tune(x64, outs, reps=tune_reps), source="autotuner")
     stream = torch.cuda.current_stream()
     res = torch.empty((64, 4), dtype=torch.float64, device=dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         B.apply(x64, outs, res)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         B.apply(x64, outs, res)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_batch = e0.elapsed_time(e1) / 1e3 / args.steps
+    t_batch = e0.elapsed_time(e1) / 1e3 / steps
     # 64 sequential FP64 launches (one pauli_expect with H psi per state)
     r128 = torch.empty((64, 4), dtype=torch.float64, device=dev)
     h128 = [torch.empty_like(p) for p in psis]
@@ -569,6 +597,7 @@ def run_batched(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1) / 1e3
+    del h128
     # and 64 sequential complex64 launches with each state's default launch shape
     r64 = torch.empty((64, 4), dtype=torch.float64, device=dev)
     for b in range(64):
@@ -581,18 +610,128 @@ def run_batched(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_seq64 = e0.elapsed_time(e1) / 1e3
     dE = (res[:, 0] - r128[:, 0]).abs().max().item()
-    line = {
-        "metric": METRIC, "value": U / t_batch, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "ms_per_step": t_batch * 1e3, "dtype": "c64/f32, f64 reductions", "data": "synthetic",
-        "config": {"workload": "64 molecules, n_orb ~ U{8..14} (seed 3), half filling, H psi + <H> per state",
-                   "sum_dim": int(sum(dims)), "max_dim": int(max(dims)), "min_dim": int(min(dims)),
-                   "updates_per_batch": U, "tuned_shape": cfg, "build_s": t_build},
+    hbm_peak, peak_kind, sm_mhz_max = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    popc_peak = sms * POPC_PER_CLK_SM * sm_mhz_max * 1e6
+    return {
+        "ms": t_batch * 1e3, "updates_per_s": U / t_batch, "popc_roof_frac": U / t_batch / popc_peak,
+        "compulsory_bytes": Bc, "hbm_frac": Bc / t_batch / 1e9 / hbm_peak,
+        "sum_dim": int(sum(dims)), "max_dim": int(max(dims)), "min_dim": int(min(dims)),
+        "updates_per_batch": U, "shape": cfg, "build_s": t_build, "steps": steps,
         "sequential_c128_ms": t_seq * 1e3, "speedup_vs_sequential_c128": t_seq / t_batch,
         "sequential_c64_ms": t_seq64 * 1e3, "speedup_vs_sequential_c64": t_seq64 / t_batch,
-        "max_energy_diff_c64_vs_c128_Ha": dE, "clocks": clk,
+        "max_energy_diff_c64_vs_c128_Ha": dE, "clocks": clk, "peak": f"{peak_kind} {hbm_peak} GB/s",
+    }
+
+
+def run_batched(args, rank, world, local_rank):
+    """The batched workload on its own (autotuned shape, seeded states)."""
+    import torch
+    import paper_2606_28952_gb300 as ps
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    r = batched_measure(ps, dev, args.warmup, args.steps)
+    line = {
+        "metric": METRIC, "value": r["updates_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "ms_per_step": r["ms"], "dtype": "c64/f32, f64 reductions", "data": "synthetic",
+        "config": {"workload": "64 molecules, n_orb ~ U{8..14} (seed 3), half filling, H psi + <H> per state",
+                   "sum_dim": r["sum_dim"], "max_dim": r["max_dim"], "min_dim": r["min_dim"],
+                   "updates_per_batch": r["updates_per_batch"], "tuned_shape": r["shape"], "build_s": r["build_s"]},
+        **{k: r[k] for k in ("sequential_c128_ms", "speedup_vs_sequential_c128", "sequential_c64_ms",
+                             "speedup_vs_sequential_c64", "max_energy_diff_c64_vs_c128_Ha", "clocks", "hbm_frac",
+                             "popc_roof_frac")},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def xxz_apply_measure(ps, dev, n: int, sz0: bool, n_lo: int = 0, warmup: int = 3, reps: int = 10,
+                      launch: str = ""):
+    """One H psi of the open XXZ chain (seed 1) on a random complex64 state, in the
+    full 2^n space or the Sz = 0 block sector; CUDA events, clocks sampled.
+    Inputs are far larger than L2 at 30 sites (8.6 GB / 1.24 GB per vector)."""
+    import torch
+    x, z, cre, cim = w.xxz_terms(n, w.XXZ_SEED)
+    H = ps.PauliSum.from_terms(n, x, z, cre, cim)
+    if not sz0:
+        S = ps.Sector.full(n, n_lo or 10)
+        label = f"xxz{n} full space 2^{n}"
+    else:
+        nl = n_lo or n // 2
+        S = ps.Sector(n, ps.BLOCKS, nl, [(k, n // 2 - k) for k in range(0, min(nl, n // 2) + 1) if n // 2 - k <= n - nl])
+        label = f"xxz{n} Sz=0 blocks, split {nl}|{n - nl}, D={S.dim}"
+    ps.prepare(H, S)
+    install_launch(ps, H, S, torch.complex64, launch)
+    U = H.m * S.dim if S.kind == ps.FULL else None
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    psi = torch.randn(S.dim, dtype=torch.complex64, device=dev, generator=gen)
+    out = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ps.apply(H, S, psi, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.2)
+    e0.record(stream)
+    for _ in range(reps):
+        ps.apply(H, S, psi, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_apply = e0.elapsed_time(e1) / 1e3 / reps
+    hbm_peak, peak_kind, _ = measured_peaks()
+    apply_bytes = 2 * S.dim * 8 + H.m * 24 + H.n_groups * 16
+    r = {"workload": label, "dim": S.dim, "terms": H.m, "groups": H.n_groups, "ms": t_apply * 1e3, "reps": reps,
+         "updates_per_s": (U / t_apply) if U else None, "compulsory_bytes": apply_bytes,
+         "achieved_gbs": apply_bytes / t_apply / 1e9, "hbm_frac": apply_bytes / t_apply / 1e9 / hbm_peak,
+         "peak": f"{peak_kind} {hbm_peak} GB/s", "launch_shape": ps.launch_config(H, S), "clocks": clk}
+    del psi, out
+    torch.cuda.empty_cache()
+    return r
+
+
+def mol32_apply_measure(ps, dev, reps: int = 2):
+    """One H psi of the 32-qubit PES molecule (16 orbitals, (8a,8b), D = 165,636,900,
+    complex64, default launch shape) at the scan's R = 1.14 point."""
+    import torch
+    norb = w.PES_NORB
+    h0, h1, g0 = w.pes_integrals(norb, w.PES_SEED)
+    h, g = w.pes_point(h0, h1, g0, w.PES_POINTS[10])
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    S = ps.Sector.molecular(norb, norb // 2, norb // 2)
+    ps.prepare(H, S)
+    xc, _, _ = H.export()
+    U = count_updates(xc, norb, norb, norb // 2, norb // 2)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(32)
+    psi = torch.randn(S.dim, dtype=torch.complex64, device=dev, generator=gen)
+    out = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    ps.apply(H, S, psi, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    for _ in range(reps):
+        ps.apply(H, S, psi, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    _, _, sm_mhz_max = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    r = {"workload": "32-qubit PES molecule, 16 orbitals, (8a,8b), D=165636900, R=1.14", "terms": H.m,
+         "groups": H.n_groups, "updates_per_apply": U, "ms": t * 1e3, "updates_per_s": U / t,
+         "popc_roof_frac": U / t / (sms * POPC_PER_CLK_SM * sm_mhz_max * 1e6),
+         "launch_shape": ps.launch_config(H, S), "clocks": clk}
+    del psi, out
+    torch.cuda.empty_cache()
+    return r
 
 
 def main():
@@ -609,6 +748,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rotate", action="store_true", help="skip the 32-qubit rotation side measurement")
+    ap.add_argument("--no-side", action="store_true", help="skip the other workloads' side measurements")
     ap.add_argument("--launch", default="", help="cols_per_thread,staged_rows,row_split,direct,ranked of the apply")
     args = ap.parse_args()
     if args.warmup < 3:

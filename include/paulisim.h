@@ -268,6 +268,35 @@ int pauli_rotate_seq(pauli_sum *const *Gs, const double *thetas, int k, const pa
 int pauli_vdot(const void *x, const void *y, int64_t n, int dtype, double *result, pauli_stream_t st);
 
 /* ------------------------------------------------------------------------- */
+/* operator-pool gradients (operator selection of ADAPT-VQE, Sec. 3.3)        */
+/* ------------------------------------------------------------------------- */
+
+/* A pool of K Hermitian single-X-group generators G_k (pauli_rotate's
+ * generator rules; the paper's anti-Hermitian pool operators are A_k = -i G_k)
+ * on one sector.  pauli_pool_create checks every generator (PAULI_EINVAL: more
+ * than one X mask; PAULI_ENOTHERMITIAN), builds or reuses each generator's
+ * pair list on a single-block sector (a one-time leak check per generator, as
+ * for pauli_rotate) and copies the tables, masks and coefficients into the
+ * pool, so the generators may be destroyed afterwards; the sector must outlive
+ * the pool.  Blocking. */
+typedef struct pauli_pool pauli_pool;
+int pauli_pool_create(pauli_sum *const *Gs, int K, const pauli_sector *s, pauli_pool **out);
+int pauli_pool_size(const pauli_pool *p, int *K);
+
+/* grads[k] = d/dtheta <psi| exp(i theta G_k) H exp(-i theta G_k) |psi> at 0
+ *          = i <psi|[G_k, H]|psi> = 2 Im <hpsi|G_k psi> = <psi|[H, A_k]|psi>,
+ * for every generator, given hpsi = H psi (the vector pauli_expect stores) on
+ * the pool's sector: G_k acts as P_S G_k P_S (a generator that moves amplitude
+ * out of the sector has its status word set to PAULI_ESECTOR, as in
+ * pauli_rotate).  grads is a DEVICE array of K doubles; psi, hpsi are device
+ * vectors of the sector's dimension in dtype, 16-byte aligned.  One launch
+ * contracts every pair-listed generator; each gradient is an FP64 sum in a
+ * fixed order (the same inputs give the same bits). */
+int pauli_pool_gradients(pauli_pool *p, const void *psi, const void *hpsi, int dtype, double *grads,
+                         pauli_stream_t st);
+int pauli_pool_destroy(pauli_pool *p);
+
+/* ------------------------------------------------------------------------- */
 /* learned warm start: a small multilayer perceptron on the tensor cores      */
 /* ------------------------------------------------------------------------- */
 

@@ -82,6 +82,10 @@ SIGNATURES = {
     "pauli_batch_set_launch_config": (_i32, [_vp, _vp]),
     "pauli_batch_get_launch_config": (_i32, [_vp, _vp]),
     "pauli_batch_destroy": (_i32, [_vp]),
+    "pauli_pool_create": (_i32, [_vp, _i32, _vp, _vp]),
+    "pauli_pool_size": (_i32, [_vp, _vp]),
+    "pauli_pool_gradients": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "pauli_pool_destroy": (_i32, [_vp]),
     "pauli_krylov_create": (_i32, [_vp, _vp, _i32, _i32, _vp]),
     "pauli_krylov_step": (_i32, [_vp, _vp, _dbl, _i32, _i32, _vp]),
     "pauli_krylov_scalars": (_i32, [_vp, _vp, _vp, _vp]),
@@ -496,6 +500,44 @@ class Krylov:
         if getattr(self, "_h", None) is not None and self._h.value:
             if _lib is not None:
                 lib().pauli_krylov_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pool:
+    """Operator pool of ADAPT-VQE: K single-X-group Hermitian generators on one
+    sector; gradients() gives dE/dtheta_k = 2 Im <H psi|G_k psi> for all k in
+    one pass (pauli_pool_gradients)."""
+
+    def __init__(self, generators, s: Sector):
+        self.s = s
+        self.K = len(generators)
+        arr = (C.c_void_p * self.K)(*[G._h.value for G in generators])
+        out = C.c_void_p()
+        _check(lib().pauli_pool_create(arr, self.K, s._h, C.byref(out)))
+        self._h = out
+
+    def gradients(self, psi, hpsi, out=None, stream=None):
+        import torch
+        _check_state(psi, self.s.dim, "psi")
+        _check_state(hpsi, self.s.dim, "hpsi")
+        if psi.dtype != hpsi.dtype:
+            raise TypeError("psi and hpsi must have the same dtype")
+        if out is None:
+            out = torch.empty(self.K, dtype=torch.float64, device=psi.device)
+        _check(lib().pauli_pool_gradients(self._h, C.c_void_p(psi.data_ptr()), C.c_void_p(hpsi.data_ptr()),
+                                          _dtype_code(psi), C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            if _lib is not None:
+                lib().pauli_pool_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -511,7 +511,7 @@ void launch_reduce(const double *partials, int64_t nparts, double *result, cudaS
     PS_LAUNCH_CHECK();
 }
 // X mask of a single-group operator, read back from the device once
-static uint64_t group_mask0(pauli_sum *G) {
+uint64_t group_mask0(pauli_sum *G) {
     if (!G->gx0_known) {
         uint64_t x = 0;
         if (G->G == 1) PS_CUDA(cudaMemcpy(&x, G->gx, sizeof(uint64_t), cudaMemcpyDeviceToHost));
@@ -595,7 +595,7 @@ static bool rotation_leaks(pauli_sum *G, const SectorView &v, uint64_t x, cudaSt
 // (the last kRotPairsCache sectors); nullptr where the per-target kernel applies:
 // full space, several blocks, x = 0, more than kRotPairTerms terms, or a generator
 // that leaks out of the sector (its leaks are then recorded on every call).
-static const RotPairs *rotation_pairs(pauli_sum *G, const pauli_sector *sec, uint64_t x, cudaStream_t st) {
+const RotPairs *rotation_pairs(pauli_sum *G, const pauli_sector *sec, uint64_t x, cudaStream_t st) {
     const SectorView &v = sec->v;
     if (v.kind != PAULI_SECTOR_BLOCKS || v.nblk != 1 || x == 0 || G->m > kRotPairTerms) return nullptr;
     for (int i = 0; i < G->nrot; ++i)

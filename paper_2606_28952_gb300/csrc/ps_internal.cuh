@@ -322,6 +322,13 @@ int64_t apply_num_ctas(const Plan &p, const SectorView &v, int dtype, bool allow
 // elements of the split scratch a launch needs (0: no split)
 int64_t apply_split_elems(const Plan &p, const SectorView &v, int dtype, const LaunchChoice *force = nullptr);
 void launch_rotate(pauli_sum *G, const pauli_sector *s, double theta, void *psi, int dtype, cudaStream_t st);
+// X mask of a single-group operator (read back once and kept in G)
+uint64_t group_mask0(pauli_sum *G);
+// Pair tables of a single-group generator on a single-block sector (built on
+// first use, with a one-time leak check that synchronises st), or nullptr where
+// the per-target kernels apply (full space, several blocks, x = 0, more than
+// kRotPairTerms terms, or a generator that leaks out of the sector).
+const RotPairs *rotation_pairs(pauli_sum *G, const pauli_sector *sec, uint64_t x, cudaStream_t st);
 // <lam|G|phi> into result[0..1] (device), then phi, lam <- exp(-i theta G) phi, lam
 void launch_rotate_adjoint(pauli_sum *G, const pauli_sector *s, double theta, void *phi, void *lam, int dtype,
                            double *result, cudaStream_t st);

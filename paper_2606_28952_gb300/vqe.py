@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import MLP, PauliSum, Sector, expect, rotate_adjoint, rotate_seq
+from . import MLP, PauliSum, Pool, Sector, expect, rotate_adjoint, rotate_seq
 
 
 # ---------------------------------------------------------------------------
@@ -259,6 +259,65 @@ def lbfgs(fg, x0, m: int = 20, gtol: float = 1e-6, ftol: float = 1e-12, patience
 # ---------------------------------------------------------------------------
 # learned warm start
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# ADAPT-VQE: operator selection by pool gradients (Sec. 3.3)
+# ---------------------------------------------------------------------------
+@dataclass
+class AdaptResult:
+    energies: list          # E after each re-optimisation (index 0: the reference)
+    selected: list          # pool indices in the order they were appended
+    grad_norms: list        # max |g_k| over the pool before each selection
+    theta: np.ndarray
+    reason: str
+
+
+def adapt_vqe(H: PauliSum, sector: Sector, pool_gens, ref_config: int, max_ops: int = 20, grad_tol: float = 1e-3,
+              dtype=None, gtol: float = 1e-7, maxiter: int = 200) -> AdaptResult:
+    """ADAPT-VQE over a pool of single-group generators: from the reference
+    configuration, repeatedly compute every pool gradient g_k = <psi|[H, A_k]|psi>
+    in one pauli_pool_gradients pass (H psi from pauli_expect), append the
+    generator with the largest |g_k| to the product ansatz (angle 0) and
+    re-optimise all angles with L-BFGS (adjoint gradients); stop when
+    max |g_k| < grad_tol or after max_ops generators."""
+    import torch
+    dtype = dtype or torch.complex128
+    ref = int(sector.rank(torch.tensor([ref_config], dtype=torch.int64, device="cuda"))[0].item())
+    if ref < 0:
+        raise ValueError("the reference configuration is not in the sector")
+    pool = Pool(pool_gens, sector)
+    psi = torch.zeros(sector.dim, dtype=dtype, device="cuda")
+    hpsi = torch.empty_like(psi)
+    res = torch.empty(4, dtype=torch.float64, device="cuda")
+    chosen, theta = [], np.zeros(0)
+    out = AdaptResult([], [], [], theta, "max_ops")
+    for it in range(max_ops + 1):
+        psi.zero_()
+        psi[ref] = 1.0
+        if chosen:
+            rotate_seq([pool_gens[k] for k in chosen], sector, theta, psi)
+        expect(H, sector, psi, hpsi_out=hpsi, result=res)
+        if it == 0:
+            out.energies.append(float(res[0].item()))
+        g = pool.gradients(psi, hpsi).cpu().numpy()
+        k = int(np.argmax(np.abs(g)))
+        out.grad_norms.append(float(abs(g[k])))
+        if abs(g[k]) < grad_tol:
+            out.reason = "grad_tol"
+            break
+        if it == max_ops:
+            break
+        chosen.append(k)
+        theta = np.concatenate([theta, [0.0]])
+        eg = EnergyGradient(H, sector, ProductAnsatz([pool_gens[j] for j in chosen], ref), dtype=dtype)
+        r = lbfgs(eg, theta, gtol=gtol, maxiter=maxiter)
+        theta = r.x
+        out.energies.append(float(r.f))
+    out.selected = chosen
+    out.theta = theta
+    pool.close()
+    return out
+
+
 def glorot_params(shapes, seed: int) -> np.ndarray:
     """Seeded initial parameter vector: uniform Glorot weights, zero biases."""
     rng = np.random.default_rng(seed)

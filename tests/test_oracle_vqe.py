@@ -67,3 +67,29 @@ def test_pair_double_generator_has_period_two_pi():
     out = oracle.rotate(s, G, np.pi / 2, e_ref)
     moved = oracle.hf_config(NORB, 2, 2) & ~((1 << p) | (1 << (NORB + p))) | (1 << q) | (1 << (NORB + q))
     assert abs(abs(out[int(s.index(moved)[0])]) - 1.0) < 1e-12
+
+
+def test_pool_gradients_match_finite_differences():
+    """ADAPT's <psi|[H, A_k]|psi> is the derivative at t = 0 of
+    <psi|exp(i t G_k) H exp(-i t G_k)|psi> (A_k = -i G_k)."""
+    _, _, H, s, _, ref, _ = _problem()
+    pool = w.uccsd_pool(NORB, 2, 2)
+    gens = [oracle.fermion_sum(2 * NORB, terms) for _, terms in pool]
+    psi = w.random_state(s.dim, 77)
+    g = vqe.pool_gradients(s, H, gens, psi)
+    step = 1e-5
+    for k, G in enumerate(gens):
+        ep = oracle.expect(s, H, oracle.rotate(s, G, step, psi))[0].real
+        em = oracle.expect(s, H, oracle.rotate(s, G, -step, psi))[0].real
+        assert abs(g[k] - (ep - em) / (2 * step)) < 1e-7, k
+    assert np.abs(g).max() > 1e-2
+
+
+def test_pool_gradient_of_a_commuting_generator_is_zero():
+    """The total particle-number-like generator sum_p n_p commutes with H: its
+    gradient vanishes for any state (pin of a dropped or mis-signed term)."""
+    _, _, H, s, _, ref, _ = _problem()
+    terms = [(1.0, [(p, 1), (p, 0)]) for p in range(2 * NORB)]
+    N = oracle.fermion_sum(2 * NORB, terms)
+    psi = w.random_state(s.dim, 78)
+    assert abs(vqe.pool_gradients(s, H, [N], psi)[0]) < 1e-12

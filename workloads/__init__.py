@@ -258,3 +258,51 @@ def pair_double_ansatz(norb: int, count: int):
     while len(out) < count:
         out.extend(base)
     return out[:count]
+
+
+def double_generator(modes_c, modes_a):
+    """G = i (T - T^dagger), T = a+_{c0} a+_{c1} a_{a1} a_{a0} (creation modes c,
+    annihilation modes a, spin-orbital indices)."""
+    c0, c1 = modes_c
+    a0, a1 = modes_a
+    return [(1j, [(c0, 1), (c1, 1), (a1, 0), (a0, 0)]),
+            (-1j, [(a0, 1), (a1, 1), (c1, 0), (c0, 0)])]
+
+
+def uccsd_pool(norb: int, na: int, nb: int, generalized: bool = False):
+    """Spin-conserving single and double excitation generators G = i (T - T^dagger)
+    of a UCCSD (or, generalized=True, UCCGSD) ansatz in blocked spin order
+    (alpha orbital r = mode r, beta orbital r = mode norb + r).
+
+    UCCSD: occupied = the lowest na alpha / nb beta orbitals, excitations from
+    occupied to virtual.  UCCGSD: every ordered pair of distinct orbital sets.
+    Order: alpha singles, beta singles, alpha-alpha doubles, beta-beta doubles,
+    alpha-beta doubles; each list lexicographic.  Returns [(label, terms)]."""
+    occ = {0: list(range(na)), 1: list(range(nb))}
+    vir = {0: list(range(na, norb)), 1: list(range(nb, norb))}
+    out = []
+    for spin in (0, 1):
+        src = range(norb) if generalized else occ[spin]
+        for p in src:
+            for q in (range(p + 1, norb) if generalized else vir[spin]):
+                out.append((f"s{'ab'[spin]}_{p}_{q}", single_generator(norb, p, q, spin)))
+    for spin in (0, 1):
+        base = spin * norb
+        if generalized:
+            pairs = [(p, q) for p in range(norb) for q in range(p + 1, norb)]
+            combos = [(a, b) for i, a in enumerate(pairs) for b in pairs[i + 1:]]
+        else:
+            op = [(i, j) for i in occ[spin] for j in occ[spin] if i < j]
+            vp = [(a, b) for a in vir[spin] for b in vir[spin] if a < b]
+            combos = [(o, v) for o in op for v in vp]
+        for (i, j), (a, b) in combos:
+            out.append((f"d{'ab'[spin]}{'ab'[spin]}_{i}{j}_{a}{b}",
+                        double_generator((base + a, base + b), (base + i, base + j))))
+    if generalized:
+        ab = [((i, j), (a, b)) for i in range(norb) for j in range(norb) for a in range(norb) for b in range(norb)
+              if (i, j) < (a, b)]
+    else:
+        ab = [((i, j), (a, b)) for i in occ[0] for j in occ[1] for a in vir[0] for b in vir[1]]
+    for (i, j), (a, b) in ab:
+        out.append((f"dab_{i}{j}_{a}{b}", double_generator((a, norb + b), (i, norb + j))))
+    return out
