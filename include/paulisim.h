@@ -258,6 +258,32 @@ int pauli_rotate_adjoint(pauli_sum *G, const pauli_sector *s, double theta, void
 int pauli_rotate_seq(pauli_sum *const *Gs, const double *thetas, int k, const pauli_sector *s, void *psi,
                      int dtype, pauli_stream_t st);
 
+/* A fixed product of single-group rotations (a Trotterised UCCSD / UCCGSD
+ * step or any product ansatz, Sec. 3.2), applied tile by tile:
+ *   psi <- exp(-i theta_{K-1} G_{K-1}) ... exp(-i theta_0 G_0) psi,
+ * every G_k with pauli_rotate's generator rules (results equal K pauli_rotate
+ * calls up to rounding; a generator that leaks out of the sector sets its
+ * status word as there).  On a single product block, consecutive generators
+ * are grouped into runs that share a tile -- generators with x_hi = 0 (and
+ * diagonal ones) into tiles of one row, generators with x_lo = 0 into tiles of
+ * all rows of a few adjacent columns, generators with one common nonzero x_hi
+ * (with row-local and diagonal ones) into tiles of the two rows r and
+ * r ^ x_hi -- and one launch per run reads and writes each tile once,
+ * applying the run's rotations in order in shared memory.  Runs whose tile
+ * exceeds shared memory, and sectors that are not one block, use one
+ * pauli_rotate launch per generator.  The generators and the sector must
+ * outlive the handle.  pauli_rotseq_create is blocking. */
+typedef struct pauli_rotseq pauli_rotseq;
+int pauli_rotseq_create(pauli_sum *const *Gs, int K, const pauli_sector *s, pauli_rotseq **out);
+
+/* thetas: HOST array of K angles, copied into the handle on st (calls with one
+ * handle must be ordered on one stream).  psi: device vector of the sector. */
+int pauli_rotseq_apply(pauli_rotseq *q, const double *thetas, void *psi, int dtype, pauli_stream_t st);
+
+/* Launches one apply makes in dtype, and how many generators run fused. */
+int pauli_rotseq_info(const pauli_rotseq *q, int dtype, int *launches, int *fused);
+int pauli_rotseq_destroy(pauli_rotseq *q);
+
 /* result[0] + i result[1] = <x|y> = sum_i conj(x_i) y_i over n amplitudes of
  * type dtype, accumulated in FP64 in a fixed order (the same inputs give the
  * same bits); result is a DEVICE array of 2 doubles written on st.  x, y

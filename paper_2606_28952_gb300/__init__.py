@@ -82,6 +82,10 @@ SIGNATURES = {
     "pauli_batch_set_launch_config": (_i32, [_vp, _vp]),
     "pauli_batch_get_launch_config": (_i32, [_vp, _vp]),
     "pauli_batch_destroy": (_i32, [_vp]),
+    "pauli_rotseq_create": (_i32, [_vp, _i32, _vp, _vp]),
+    "pauli_rotseq_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "pauli_rotseq_info": (_i32, [_vp, _i32, _vp, _vp]),
+    "pauli_rotseq_destroy": (_i32, [_vp]),
     "pauli_pool_create": (_i32, [_vp, _i32, _vp, _vp]),
     "pauli_pool_size": (_i32, [_vp, _vp]),
     "pauli_pool_gradients": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
@@ -500,6 +504,48 @@ class Krylov:
         if getattr(self, "_h", None) is not None and self._h.value:
             if _lib is not None:
                 lib().pauli_krylov_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RotSeq:
+    """A fixed product of single-group rotations applied tile by tile
+    (pauli_rotseq_*): apply(thetas, psi) = rotate_seq(gens, s, thetas, psi)."""
+
+    def __init__(self, generators, s: Sector):
+        self.s = s
+        self.gens = list(generators)  # kept alive with the handle
+        self.K = len(self.gens)
+        arr = (C.c_void_p * self.K)(*[G._h.value for G in self.gens])
+        out = C.c_void_p()
+        _check(lib().pauli_rotseq_create(arr, self.K, s._h, C.byref(out)))
+        self._h = out
+
+    def apply(self, thetas, psi, stream=None):
+        _check_state(psi, self.s.dim, "psi")
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(-1))
+        if th.size != self.K:
+            raise ValueError(f"expected {self.K} angles, got {th.size}")
+        _check(lib().pauli_rotseq_apply(self._h, _np_ptr(th), C.c_void_p(psi.data_ptr()), _dtype_code(psi),
+                                        _stream_ptr(stream)))
+        return psi
+
+    def info(self, dtype=None):
+        import torch
+        code = C64 if dtype in (None, torch.complex64) else C128
+        nl, nf = C.c_int(), C.c_int()
+        _check(lib().pauli_rotseq_info(self._h, code, C.byref(nl), C.byref(nf)))
+        return {"launches": nl.value, "fused": nf.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            if _lib is not None:
+                lib().pauli_rotseq_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

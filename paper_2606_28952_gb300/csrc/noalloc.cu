@@ -72,6 +72,11 @@ extern "C" int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const v
         Plan *p = find_plan(H, s->v);
         PS_CHECK(p != nullptr, PAULI_EINVAL,
                  "no apply plan for this sector split: call pauli_prepare(H, s) once before pauli_expect_noalloc");
+        // one CTA per (row, column tile), no split: the launch touches no scratch but the static array
+        const int64_t nct = apply_num_ctas(*p, s->v, dtype, false);
+        PS_CHECK(nct <= kNoallocMaxBlocks, PAULI_EUNSUPPORTED,
+                 "pauli_expect_noalloc: this sector needs " + std::to_string(nct) +
+                     " thread blocks of partial sums; the static scratch holds " + std::to_string(kNoallocMaxBlocks));
         // the full-space pass kernel accumulates H psi across its passes: without an
         // output vector it would use (and on first use allocate) the plan's own
         // dim-sized scratch, so that case needs hpsi_out or an existing scratch
@@ -80,11 +85,6 @@ extern "C" int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const v
             PS_CHECK(local_scratch_bytes(p->local) >= (int64_t)bytes, PAULI_EUNSUPPORTED,
                      "pauli_expect_noalloc: this full-space operator is applied in passes that accumulate H psi in "
                      "a vector; pass hpsi_out (a dim-sized vector) or call pauli_expect once without it first");
-        // one CTA per (row, column tile), no split: the launch touches no scratch but the static array
-        const int64_t nct = apply_num_ctas(*p, s->v, dtype, false);
-        PS_CHECK(nct <= kNoallocMaxBlocks, PAULI_EUNSUPPORTED,
-                 "pauli_expect_noalloc: this sector needs " + std::to_string(nct) +
-                     " thread blocks of partial sums; the static scratch holds " + std::to_string(kNoallocMaxBlocks));
         cudaStream_t cs = (cudaStream_t)st;
         if (nct == 0) {
             PS_CUDA(cudaMemsetAsync(result, 0, 4 * sizeof(double), cs));

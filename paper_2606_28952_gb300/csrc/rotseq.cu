@@ -1,0 +1,463 @@
+// rotseq.cu -- products of single-group rotations applied tile by tile
+// (Trotterised UCCSD / UCCGSD and other product ansatze, Sec. 3.2: the
+// "Trotter" column of Table 2).
+//
+//   psi <- U_{K-1} ... U_1 U_0 psi,   U_k = exp(-i theta_k G_k),
+// every G_k Hermitian with one X mask x_k (pauli_rotate's generator).  On a
+// single product block the index of t = (t_hi, t_lo) is off + rank(t_hi) D_lo +
+// rank(t_lo): a row per high string, a column per low string.  A generator
+// whose x_hi is 0 pairs targets inside one row; one whose x_lo is 0 pairs them
+// inside one column; any other pairs row t_hi with row t_hi ^ x_hi.  The
+// sequence is cut into runs of consecutive generators that share a tile
+// shape, each run applied by one launch in which a CTA
+//   1. loads its tile of psi into shared memory,
+//   2. applies every rotation of the run in order on the tile (a barrier
+//      between rotations; each pair {t, t ^ x} is updated by one thread),
+//   3. writes the tile back,
+// so psi is read and written once per run instead of once per rotation:
+//   ROW  runs (x_hi = 0, and diagonal generators): tile = one row;
+//   COL  runs (x_lo = 0, and diagonal generators): tile = every row of a
+//        block of a few adjacent columns (64-byte row segments);
+//   PAIR runs (one common x_hi != 0, with row-local and diagonal generators):
+//        tile = the rows {r, r ^ x_hi} (or r alone when r ^ x_hi is outside
+//        the sector; such rows are skipped when no generator of the run acts
+//        inside one row).
+// Runs whose tile does not fit in shared memory (or sectors that are not one
+// product block) fall back to one pauli_rotate launch per generator.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "apply_kernels.cuh"
+
+namespace ps {
+namespace {
+
+enum : int { RS_ROW = 0, RS_COL = 1, RS_PAIR = 2, RS_EACH = 3 };
+constexpr int kSeqThreads = 512;
+
+struct SeqGen {
+    uint64_t x;
+    int t0, t1;    // terms of the generator in the sequence's term arrays
+    int theta;     // index into the angle array
+    int b0;        // lowest set bit of x (-1 for x = 0)
+    int *status;   // the generator's device status word (sector leaks)
+    int pad;
+};
+
+struct SeqArgs {
+    const SeqGen *gens;
+    int g0, g1;                 // generators of this run
+    const uint64_t *tz;         // [terms] Z masks of the whole sequence
+    const double2 *tc;          // [terms] XZ-form coefficients
+    const double *theta;        // [K] angles (device)
+    uint64_t xh;                // PAIR: the run's common x_hi
+    int width;                  // COL: columns per tile
+    int has_local;              // PAIR: a generator of the run acts inside one row
+};
+
+template <typename R>
+__device__ __forceinline__ void phase_sum(const SeqArgs &a, const SeqGen &g, uint64_t s, R &fr, R &fi) {
+    for (int k = g.t0; k < g.t1; ++k) {
+        const uint32_t par = __popcll(__ldg(a.tz + k) & s);
+        const double2 c = __ldg(a.tc + k);
+        fr += flip((R)c.x, par);
+        fi += flip((R)c.y, par);
+    }
+}
+
+template <typename R> __device__ __forceinline__ void sincos_s(R a, R *s, R *c);
+template <> __device__ __forceinline__ void sincos_s<float>(float a, float *s, float *c) { sincosf(a, s, c); }
+template <> __device__ __forceinline__ void sincos_s<double>(double a, double *s, double *c) { sincos(a, s, c); }
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kSeqThreads)
+k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
+    using C2 = typename Cx<R>::T;
+    extern __shared__ __align__(16) char smem[];
+    C2 *tile = reinterpret_cast<C2 *>(smem);
+    const int tid = threadIdx.x;
+    const int klo = v.klo[0], khi = v.khi[0];
+    const int64_t dlo = v.dlo[0], off = v.off[0];
+    const uint32_t *lst_lo = v.list_lo + v.list_lo_off[klo];
+    const uint32_t *lst_hi = v.list_hi + v.list_hi_off[khi];
+    const uint32_t lomask = (uint32_t)((1ull << v.n_lo) - 1ull);
+    int nrow = 1;
+    int64_t ncol = dlo, c0 = 0;
+    uint32_t rpat[2] = {0u, 0u};
+    int64_t rrank[2] = {0, 0};
+    if (MODE == RS_COL) {
+        c0 = (int64_t)blockIdx.x * A.width;
+        ncol = min((int64_t)A.width, dlo - c0);
+        nrow = (int)v.dhi[0];
+    } else {
+        const int64_t i = blockIdx.x;
+        rpat[0] = __ldg(lst_hi + i);
+        rrank[0] = i;
+        if (MODE == RS_PAIR) {
+            const uint32_t r2 = rpat[0] ^ (uint32_t)A.xh;
+            if (__popc(r2) == khi) {
+                const int64_t j = __ldg(v.rank_hi + r2);
+                if (j < i) return;  // the partner row's block owns this pair of rows
+                rpat[1] = r2;
+                rrank[1] = j;
+                nrow = 2;
+            } else if (!A.has_local) {
+                return;  // no generator of the run acts on a row whose partner is outside the sector
+            }
+        }
+    }
+    const int64_t nent = (int64_t)nrow * ncol;
+    // 1. the tile -> shared memory (rows are contiguous runs of ncol amplitudes)
+    for (int64_t e = tid; e < nent; e += kSeqThreads) {
+        const int64_t rs = e / ncol, cc = e - rs * ncol;
+        const int64_t rowrank = (MODE == RS_COL) ? rs : rrank[rs];
+        tile[e] = psi[off + rowrank * dlo + c0 + cc];
+    }
+    __syncthreads();
+    // 2. the run's rotations, in order
+    for (int gi = A.g0; gi < A.g1; ++gi) {
+        const SeqGen g = A.gens[gi];
+        const R theta = (R)__ldg(A.theta + g.theta);
+        for (int64_t e = tid; e < nent; e += kSeqThreads) {
+            const int64_t rs = e / ncol, cc = e - rs * ncol;
+            const uint32_t thi = (MODE == RS_COL) ? __ldg(lst_hi + rs) : rpat[rs];
+            const uint32_t tlo = __ldg(lst_lo + c0 + cc);
+            const uint64_t t = (uint64_t)tlo | ((uint64_t)thi << v.n_lo);
+            R fr = R(0), fi = R(0);
+            if (g.x == 0) {
+                // exp(-i theta f_t) on one amplitude (f real for a Hermitian diagonal generator)
+                phase_sum<R>(A, g, t, fr, fi);
+                R sn, cs;
+                sincos_s<R>(theta * fr, &sn, &cs);
+                const C2 a = tile[e];
+                C2 o;
+                o.x = cs * a.x + sn * a.y;
+                o.y = cs * a.y - sn * a.x;
+                tile[e] = o;
+                continue;
+            }
+            if (!((t >> g.b0) & 1ull)) continue;  // each pair from its member with bit b0 set
+            const uint64_t s = t ^ g.x;
+            const uint32_t slo = (uint32_t)(s & lomask), shi = (uint32_t)(s >> v.n_lo);
+            phase_sum<R>(A, g, s, fr, fi);
+            bool in = __popc(slo) == klo && __popc(shi) == khi;
+            int64_t pe = 0;
+            if (in) {
+                if (MODE == RS_COL) {
+                    pe = (int64_t)__ldg(v.rank_hi + shi) * ncol + cc;
+                } else {
+                    int64_t prs = rs;
+                    if (shi != thi) prs = (nrow == 2 && shi == rpat[rs ^ 1]) ? (rs ^ 1) : -1;
+                    if (prs < 0) in = false;
+                    else pe = prs * ncol + (int64_t)__ldg(v.rank_lo + slo);
+                }
+            }
+            if (!in) {
+                if (fr != R(0) || fi != R(0)) atomicCAS(g.status, 0, (int)PAULI_ESECTOR);
+                continue;
+            }
+            const R mag = sqrt(fr * fr + fi * fi);
+            if (mag == R(0)) continue;
+            R sn, cs;
+            sincos_s<R>(theta * mag, &sn, &cs);
+            const R q = sn / mag;
+            const C2 a = tile[e], b = tile[pe];
+            const R wr = fr * b.x - fi * b.y, wi = fr * b.y + fi * b.x;   // f b
+            const R ur = fr * a.x + fi * a.y, ui = fr * a.y - fi * a.x;   // conj(f) a
+            C2 na, nb;
+            na.x = cs * a.x + q * wi;
+            na.y = cs * a.y - q * wr;
+            nb.x = cs * b.x + q * ui;
+            nb.y = cs * b.y - q * ur;
+            tile[e] = na;
+            tile[pe] = nb;
+        }
+        __syncthreads();
+    }
+    // 3. the tile -> psi
+    for (int64_t e = tid; e < nent; e += kSeqThreads) {
+        const int64_t rs = e / ncol, cc = e - rs * ncol;
+        const int64_t rowrank = (MODE == RS_COL) ? rs : rrank[rs];
+        psi[off + rowrank * dlo + c0 + cc] = tile[e];
+    }
+}
+
+}  // namespace
+}  // namespace ps
+
+using namespace ps;
+
+struct pauli_rotseq {
+    uint32_t magic;
+    Allocator al;
+    int K = 0;
+    const pauli_sector *s = nullptr;   // must outlive the sequence
+    std::vector<pauli_sum *> G;        // generators (must outlive the sequence; used by the fallback)
+    struct Run {
+        int mode;       // RS_ROW / RS_COL / RS_PAIR (fused) or RS_EACH (one pauli_rotate per generator)
+        int g0, g1;
+        uint64_t xh;
+        int has_local;
+    };
+    std::vector<Run> runs;
+    std::vector<int> rec_theta;        // angle index of each generator record (fallback launches)
+    SeqGen *d_gens = nullptr;
+    uint64_t *d_tz = nullptr;
+    double2 *d_tc = nullptr;
+    double *d_theta = nullptr;
+};
+
+namespace {
+constexpr uint32_t kSeqMagic = 0x50525331u;  // "PRS1"
+
+void free_seq(pauli_rotseq *q) {
+    if (!q) return;
+    dev_free(q->al, q->d_gens);
+    dev_free(q->al, q->d_tz);
+    dev_free(q->al, q->d_tc);
+    dev_free(q->al, q->d_theta);
+    q->magic = 0;
+    delete q;
+}
+
+// columns of a COL tile: 64-byte row segments, fewer if every row does not fit
+int64_t col_width(const SectorView &v, size_t es) {
+    const int64_t want = (int64_t)(64 / es);
+    const int64_t fit = (int64_t)(226 * 1024 / (es * (size_t)std::max<int64_t>(1, v.dhi[0])));
+    return std::min<int64_t>({want, fit, v.dlo[0]});
+}
+
+size_t run_smem(const pauli_rotseq::Run &r, const SectorView &v, size_t es) {
+    if (r.mode == RS_ROW) return (size_t)v.dlo[0] * es;
+    if (r.mode == RS_PAIR) return 2 * (size_t)v.dlo[0] * es;
+    const int64_t w = col_width(v, es);
+    return w < 1 ? SIZE_MAX : (size_t)v.dhi[0] * (size_t)w * es;
+}
+
+template <typename R>
+void launch_run(const pauli_rotseq *q, const pauli_rotseq::Run &r, void *psi, cudaStream_t st) {
+    using C2 = typename Cx<R>::T;
+    const SectorView &v = q->s->v;
+    const size_t es = sizeof(C2);
+    SeqArgs A;
+    A.gens = q->d_gens;
+    A.g0 = r.g0;
+    A.g1 = r.g1;
+    A.tz = q->d_tz;
+    A.tc = q->d_tc;
+    A.theta = q->d_theta;
+    A.xh = r.xh;
+    A.width = (int)col_width(v, es);
+    A.has_local = r.has_local;
+    const size_t smem = run_smem(r, v, es);
+    C2 *p = static_cast<C2 *>(psi);
+    auto go = [&](auto kern, int64_t grid) {
+        if (grid <= 0) return;
+        PS_CHECK(grid < (1ll << 31), PAULI_EUNSUPPORTED, "rotation sequence: too many tiles");
+        smem_optin(reinterpret_cast<const void *>(kern), smem);
+        kern<<<(unsigned)grid, kSeqThreads, smem, st>>>(v, A, p);
+        PS_LAUNCH_CHECK();
+    };
+    if (r.mode == RS_ROW) go(k_rotseq<R, RS_ROW>, v.dhi[0]);
+    else if (r.mode == RS_PAIR) go(k_rotseq<R, RS_PAIR>, v.dhi[0]);
+    else go(k_rotseq<R, RS_COL>, (v.dlo[0] + A.width - 1) / A.width);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pauli_rotseq_create(pauli_sum *const *Gs, int K, const pauli_sector *s, pauli_rotseq **out) {
+    pauli_rotseq *q = nullptr;
+    try {
+        clear_error();
+        PS_CHECK(out != nullptr, PAULI_EINVAL, "out is NULL");
+        *out = nullptr;
+        PS_CHECK(K >= 1 && K <= (1 << 22), PAULI_EINVAL, "K must be in 1..4194304");
+        PS_CHECK(Gs != nullptr, PAULI_EINVAL, "Gs is NULL");
+        PS_CHECK(s != nullptr && s->magic == kSectorMagic, PAULI_EINVAL, "not a valid pauli_sector handle");
+        for (int k = 0; k < K; ++k) {
+            PS_CHECK(Gs[k] != nullptr && Gs[k]->magic == kSumMagic, PAULI_EINVAL,
+                     "sequence: generator " + std::to_string(k) + " is not a valid pauli_sum handle");
+            PS_CHECK(Gs[k]->n == s->v.n, PAULI_EINVAL, "sequence: generator and sector qubit counts differ");
+            PS_CHECK(Gs[k]->m == 0 || Gs[k]->G == 1, PAULI_EINVAL,
+                     "sequence: generator " + std::to_string(k) + " must have exactly one X mask");
+            PS_CHECK(Gs[k]->hermitian, PAULI_ENOTHERMITIAN,
+                     "sequence: generator " + std::to_string(k) + " is not Hermitian");
+        }
+        q = new pauli_rotseq();
+        q->magic = kSeqMagic;
+        q->al = current_allocator();
+        q->K = K;
+        q->s = s;
+        q->G.assign(Gs, Gs + K);
+        const SectorView &v = s->v;
+        const bool single = v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1;
+        // generator records and the terms of every generator (copied from the handles)
+        std::vector<SeqGen> gens;
+        std::vector<uint64_t> tz;
+        std::vector<double2> tc;
+        std::vector<int> gen_of;  // sequence position -> record (-1: empty generator)
+        for (int k = 0; k < K; ++k) {
+            pauli_sum *G = Gs[k];
+            if (G->m == 0) {
+                gen_of.push_back(-1);
+                continue;
+            }
+            const uint64_t x = group_mask0(G);
+            std::vector<uint64_t> hz(G->m);
+            std::vector<double2> hc(G->m);
+            PS_CUDA(cudaMemcpy(hz.data(), G->z, G->m * 8, cudaMemcpyDeviceToHost));
+            PS_CUDA(cudaMemcpy(hc.data(), G->c, G->m * 16, cudaMemcpyDeviceToHost));
+            SeqGen g;
+            g.x = x;
+            g.t0 = (int)tz.size();
+            tz.insert(tz.end(), hz.begin(), hz.end());
+            tc.insert(tc.end(), hc.begin(), hc.end());
+            g.t1 = (int)tz.size();
+            g.theta = k;
+            g.b0 = x ? __builtin_ctzll(x) : -1;
+            g.status = G->status;
+            g.pad = 0;
+            gen_of.push_back((int)gens.size());
+            gens.push_back(g);
+        }
+        // runs over the records, in sequence order
+        const uint64_t lomask = (1ull << v.n_lo) - 1ull;
+        pauli_rotseq::Run cur{-1, 0, 0, 0, 0};
+        auto flush = [&]() {
+            if (cur.mode >= 0 && cur.g1 > cur.g0) q->runs.push_back(cur);
+        };
+        for (int r = 0; r < (int)gens.size(); ++r) {
+            const uint64_t x = gens[r].x, xl = x & lomask, xhh = x >> v.n_lo;
+            if (!single) {
+                if (cur.mode != RS_EACH) {
+                    flush();
+                    cur = {RS_EACH, r, r, 0, 0};
+                }
+                cur.g1 = r + 1;
+                continue;
+            }
+            int mode;
+            if (x == 0) mode = cur.mode >= 0 && cur.mode != RS_EACH ? cur.mode : RS_ROW;  // joins any run
+            else if (xhh == 0) mode = (cur.mode == RS_PAIR) ? RS_PAIR : RS_ROW;
+            else if (xl == 0) mode = RS_COL;
+            else mode = RS_PAIR;
+            const bool local = x == 0 || xhh == 0;
+            bool joins = false;
+            if (cur.mode == mode && mode != RS_PAIR) joins = true;
+            if (mode == RS_PAIR && cur.mode == RS_PAIR && (xhh == 0 || xhh == cur.xh || x == 0)) joins = true;
+            if (mode == RS_PAIR && cur.mode == RS_ROW && xhh != 0) {
+                // a row run becomes a row-pair run: its generators act inside each row of the pair
+                cur.mode = RS_PAIR;
+                cur.xh = xhh;
+                cur.has_local = 1;
+                joins = true;
+            }
+            if (!joins) {
+                flush();
+                cur = {mode, r, r, mode == RS_PAIR ? xhh : 0, 0};
+            }
+            if (cur.mode == RS_PAIR && local) cur.has_local = 1;
+            cur.g1 = r + 1;
+        }
+        flush();
+        for (const SeqGen &g : gens) q->rec_theta.push_back(g.theta);
+        // device copies
+        q->d_gens = static_cast<SeqGen *>(dev_alloc(q->al, std::max<size_t>(1, gens.size()) * sizeof(SeqGen)));
+        q->d_tz = static_cast<uint64_t *>(dev_alloc(q->al, std::max<size_t>(1, tz.size()) * 8));
+        q->d_tc = static_cast<double2 *>(dev_alloc(q->al, std::max<size_t>(1, tc.size()) * 16));
+        q->d_theta = static_cast<double *>(dev_alloc(q->al, (size_t)K * sizeof(double)));
+        if (!gens.empty()) PS_CUDA(cudaMemcpy(q->d_gens, gens.data(), gens.size() * sizeof(SeqGen), cudaMemcpyHostToDevice));
+        if (!tz.empty()) {
+            PS_CUDA(cudaMemcpy(q->d_tz, tz.data(), tz.size() * 8, cudaMemcpyHostToDevice));
+            PS_CUDA(cudaMemcpy(q->d_tc, tc.data(), tc.size() * 16, cudaMemcpyHostToDevice));
+        }
+        // the generator of each record, for the fallback launches
+        q->G.clear();
+        for (int k = 0; k < K; ++k)
+            if (gen_of[k] >= 0) q->G.push_back(Gs[k]);
+        *out = q;
+        return PAULI_OK;
+    } catch (const Error &e) {
+        free_seq(q);
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        free_seq(q);
+        set_error("unexpected internal error");
+        return PAULI_EINVAL;
+    }
+}
+
+int pauli_rotseq_info(const pauli_rotseq *q, int dtype, int *launches, int *fused) {
+    try {
+        clear_error();
+        PS_CHECK(q && q->magic == kSeqMagic, PAULI_EINVAL, "not a valid pauli_rotseq handle");
+        PS_CHECK(dtype == PAULI_C64 || dtype == PAULI_C128, PAULI_EINVAL, "bad dtype");
+        const size_t es = dtype == PAULI_C64 ? 8 : 16;
+        int nl = 0, nf = 0;
+        for (const auto &r : q->runs) {
+            if (r.mode != RS_EACH && run_smem(r, q->s->v, es) <= 226 * 1024) {
+                ++nl;
+                nf += r.g1 - r.g0;
+            } else {
+                nl += r.g1 - r.g0;
+            }
+        }
+        if (launches) *launches = nl;
+        if (fused) *fused = nf;
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    }
+}
+
+int pauli_rotseq_apply(pauli_rotseq *q, const double *thetas, void *psi, int dtype, pauli_stream_t st) {
+    try {
+        clear_error();
+        PS_CHECK(q && q->magic == kSeqMagic, PAULI_EINVAL, "not a valid pauli_rotseq handle");
+        PS_CHECK(q->s->magic == kSectorMagic, PAULI_EINVAL, "the sequence's sector has been destroyed");
+        PS_CHECK(dtype == PAULI_C64 || dtype == PAULI_C128, PAULI_EINVAL, "bad dtype");
+        PS_CHECK(thetas != nullptr, PAULI_EINVAL, "thetas is NULL");
+        PS_CHECK(psi && ((uintptr_t)psi % 16) == 0, PAULI_EINVAL, "psi is NULL or not 16-byte aligned");
+        for (int k = 0; k < q->K; ++k) PS_CHECK(std::isfinite(thetas[k]), PAULI_EINVAL, "thetas must be finite");
+        cudaStream_t cs = (cudaStream_t)st;
+        // the angles: one host-to-device copy into the handle (calls with one handle
+        // must be ordered; the copy is staged before this call returns)
+        PS_CUDA(cudaMemcpyAsync(q->d_theta, thetas, (size_t)q->K * sizeof(double), cudaMemcpyHostToDevice, cs));
+        const size_t es = dtype == PAULI_C64 ? 8 : 16;
+        for (const auto &run : q->runs) {
+            if (run.mode != RS_EACH && run_smem(run, q->s->v, es) <= 226 * 1024) {
+                if (dtype == PAULI_C64) launch_run<float>(q, run, psi, cs);
+                else launch_run<double>(q, run, psi, cs);
+                continue;
+            }
+            // records keep the sequence order of the non-empty generators
+            for (int r = run.g0; r < run.g1; ++r) launch_rotate(q->G[r], q->s, thetas[q->rec_theta[r]], psi, dtype, cs);
+        }
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PAULI_EINVAL;
+    }
+}
+
+int pauli_rotseq_destroy(pauli_rotseq *q) {
+    if (!q) return PAULI_OK;
+    if (q->magic != kSeqMagic) {
+        set_error("not a valid pauli_rotseq handle");
+        return PAULI_EINVAL;
+    }
+    clear_error();
+    free_seq(q);
+    return PAULI_OK;
+}
+
+}  // extern "C"

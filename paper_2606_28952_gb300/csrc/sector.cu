@@ -17,17 +17,20 @@ namespace ps {
 namespace {
 
 __constant__ uint64_t c_binom[33][33];  // C(p, j) for 0 <= p, j <= 32
-bool g_binom_ready = false;
+constexpr int kBinomDevices = 64;
+bool g_binom_ready[kBinomDevices] = {};  // constant memory is per device
 
 void ensure_binom() {
-    if (g_binom_ready) return;
+    int dev = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < kBinomDevices && g_binom_ready[dev]) return;
     uint64_t b[33][33] = {};
     for (int p = 0; p <= 32; ++p) {
         b[p][0] = 1;
         for (int j = 1; j <= p; ++j) b[p][j] = b[p - 1][j - 1] + (j <= p - 1 ? b[p - 1][j] : 0);
     }
     PS_CUDA(cudaMemcpyToSymbol(c_binom, b, sizeof(b)));
-    g_binom_ready = true;
+    if (dev >= 0 && dev < kBinomDevices) g_binom_ready[dev] = true;
 }
 
 __device__ __forceinline__ uint64_t colex_rank(uint32_t s) {

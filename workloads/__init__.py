@@ -306,3 +306,20 @@ def uccsd_pool(norb: int, na: int, nb: int, generalized: bool = False):
     for (i, j), (a, b) in ab:
         out.append((f"dab_{i}{j}_{a}{b}", double_generator((a, norb + b), (i, norb + j))))
     return out
+
+
+def uccsd_trotter_order(pool, norb: int):
+    """One Trotter step's factor order for a UCCSD / UCCGSD pool: the alpha-only
+    generators (singles, then doubles), the beta-only ones, then the alpha-beta
+    doubles grouped by their beta excitation (the pool's labels give the spin
+    cases; a product formula may take its factors in any fixed order)."""
+    def key(item):
+        label, terms = item
+        kind = label.split("_")[0]
+        if kind in ("sa", "daa"):
+            return (0, 0)
+        if kind in ("sb", "dbb"):
+            return (1, 0)
+        modes = sorted({m for m, _ in terms[0][1] if m >= norb})
+        return (2, tuple(modes))
+    return sorted(pool, key=key)  # stable: the pool's order inside each class
