@@ -185,6 +185,7 @@ void check_integrals(int norb, const double *h, const double *g) {
 Plan &ensure_plan(pauli_sum *H, const pauli_sector *s, cudaStream_t st, bool need_partials) {
     Plan &p = get_plan(H, s->v, st);
     prepare_for_sector(H, p, s->v, st);
+    ensure_df_capacity(H, p, s->v, st);
     // partial vectors of split launches (the split count depends on the dtype:
     // sized for both, so that either precision can run on the same plan)
     const int64_t split_bytes = std::max(apply_split_elems(p, s->v, PAULI_C64) * 8,

@@ -502,6 +502,7 @@ void free_plan(const Allocator &al, Plan &p) {
     free_lists(al, p);
     dev_free(al, p.partials);
     dev_free(al, p.split_buf);
+    dev_free(al, p.df_buf);
     p = Plan();
 }
 

@@ -136,10 +136,110 @@ __device__ __forceinline__ void list_unit(const Buf<R> &B, const int4 e, const u
     }
 }
 
-template <typename R, bool REALH>
+// ---------------------------------------------------------------------------
+// complex128 in double-float arithmetic.  FP64 runs at a small fraction of the
+// FP32 rate on this GPU, and the segment sums and accumulations of the gather
+// are its inner loop.  The complex128 path therefore reads psi as hi + lo
+// FP32 pairs (split once per apply by k_split_df: hi = fl32(v), lo =
+// fl32(v - hi), 48 significant bits), keeps the folded segment coefficients
+// and the accumulators as hi + lo pairs, and sums with Knuth's TwoSum and
+// products split exactly with FMA (Dekker); the fold of the high-half phases
+// and the epilogue stay FP64.
+// ---------------------------------------------------------------------------
+__global__ void k_split_df(const double2 *__restrict__ v, float4 *__restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 a = v[i];
+    const float hr = __double2float_rn(a.x), hi = __double2float_rn(a.y);
+    out[i] = make_float4(hr, hi, __double2float_rn(a.x - (double)hr), __double2float_rn(a.y - (double)hi));
+}
+
+// (ph, pl) = (fh + fl) * (ah + al) to about 2^-47 relative: the product of the
+// high parts split exactly by FMA, plus the two cross terms (fl * al dropped)
+__device__ __forceinline__ void df_mul(float fh, float fl, float ah, float al, float &ph, float &pl) {
+    ph = __fmul_rn(fh, ah);
+    const float e = __fmaf_rn(fh, ah, -ph);
+    pl = __fmaf_rn(fh, al, __fmaf_rn(fl, ah, e));
+}
+
+// (h, l) += (ph, pl), renormalised so that |l| <= ulp(h) / 2
+__device__ __forceinline__ void df_add(float &h, float &l, float ph, float pl) {
+    float s, e;
+    two_sum(h, ph, s, e);
+    const float t = __fadd_rn(__fadd_rn(l, pl), e);
+    const float hh = __fadd_rn(s, t);
+    l = __fsub_rn(t, __fsub_rn(hh, s));
+    h = hh;
+}
+
+// list_unit of the complex128 path: row and segment coefficients as float4
+// {re hi, im hi, re lo, im lo}, accumulator row likewise.
+template <bool REALH>
+__device__ __forceinline__ void list_unit_df(const float4 *__restrict__ row, const float4 *__restrict__ a4,
+                                             const uint32_t *__restrict__ zs, const int4 e,
+                                             const uint32_t *__restrict__ ent, int len, int base, int lane,
+                                             float4 *my) {
+    uint32_t w[kListK];
+    bool ok[kListK];
+#pragma unroll
+    for (int k = 0; k < kListK; ++k) {
+        const int i = base + lane + 32 * k;
+        ok[k] = i < len;
+        w[k] = ok[k] ? __ldg(ent + i) : 0u;
+    }
+    uint32_t s[kListK];
+    float4 amp[kListK];
+    float frh[kListK], frl[kListK], fih[kListK], fil[kListK];
+#pragma unroll
+    for (int k = 0; k < kListK; ++k) {
+        s[k] = (w[k] >> 20) ^ (uint32_t)e.x;
+        amp[k] = row[(w[k] >> 10) & 1023u];
+        frh[k] = frl[k] = fih[k] = fil[k] = 0.f;
+    }
+    // f = sum over the item's segments of +-a_seg: TwoSum on the high parts, the
+    // rounding errors and the low parts summed beside them
+    for (int sg = e.y; sg < e.z; ++sg) {
+        const uint32_t z = zs[sg];
+        const float4 a = a4[sg];
+#pragma unroll
+        for (int k = 0; k < kListK; ++k) {
+            const uint32_t par = __popc(z & s[k]);
+            float t, err;
+            two_sum(frh[k], flip(a.x, par), t, err);
+            frh[k] = t;
+            frl[k] = __fadd_rn(frl[k], __fadd_rn(err, flip(a.z, par)));
+            if (!REALH) {
+                two_sum(fih[k], flip(a.y, par), t, err);
+                fih[k] = t;
+                fil[k] = __fadd_rn(fil[k], __fadd_rn(err, flip(a.w, par)));
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kListK; ++k) {
+        if (!ok[k]) continue;
+        float4 &o = my[w[k] & 1023u];
+        float4 t = o;
+        float ph, pl;
+        df_mul(frh[k], frl[k], amp[k].x, amp[k].z, ph, pl);  // f_re a_re
+        df_add(t.x, t.z, ph, pl);
+        df_mul(frh[k], frl[k], amp[k].y, amp[k].w, ph, pl);  // f_re a_im
+        df_add(t.y, t.w, ph, pl);
+        if (!REALH) {
+            df_mul(fih[k], fil[k], amp[k].y, amp[k].w, ph, pl);  // - f_im a_im
+            df_add(t.x, t.z, -ph, -pl);
+            df_mul(fih[k], fil[k], amp[k].x, amp[k].z, ph, pl);  // + f_im a_re
+            df_add(t.y, t.w, ph, pl);
+        }
+        o = t;
+    }
+}
+
+template <typename R, bool REALH, bool DF>
 __global__ void __launch_bounds__(kListThreads)
 k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>::T *__restrict__ psi,
-             typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
+             const float4 *__restrict__ psi_df, typename Cx<R>::T *__restrict__ out, double *__restrict__ partials,
+             int flags) {
     using C2 = typename Cx<R>::T;
     extern __shared__ __align__(16) char smem[];
     const int64_t dlo = v.dlo[0];
@@ -161,8 +261,11 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
     int unused = 0;
     const int pend = geo.split_p0[rc.split + 1];
     int q = next_piece<R, KBLKR>(v, p, geo.split_p0[rc.split] - 1, rc.thi, pend);
+    // the double-float path stages rows of the hi / lo split of psi (16 bytes per
+    // amplitude, like complex128)
+    const C2 *src = DF ? reinterpret_cast<const C2 *>(psi_df) : psi;
     while (q < pend) {
-        stage_piece<R, KBLKR, REALH>(v, p, q, rc.thi, psi, B, &unused);
+        stage_piece<R, KBLKR, REALH>(v, p, q, rc.thi, src, B, &unused);
         const int i0 = __ldg(p.pc_i0 + q), i1 = __ldg(p.pc_i0 + q + 1);
         for (int it = i0 + tid; it < i1; it += kListThreads) {
             const int l = __ldg(L.it_list + it);
@@ -171,6 +274,17 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
         }
         cp_async_wait<0>();
         __syncthreads();
+        if (DF) {
+            // the folded FP64 segment coefficients -> hi / lo FP32 pairs, in place
+            const int nseg = __ldg(p.it_s0 + i1) - __ldg(p.it_s0 + i0);
+            float4 *a4 = reinterpret_cast<float4 *>(B.a);
+            for (int sg = tid; sg < nseg; sg += kListThreads) {
+                const C2 a = B.a[sg];
+                const float hr = (float)a.x, hi = (float)a.y;
+                a4[sg] = make_float4(hr, hi, (float)(a.x - (double)hr), (float)(a.y - (double)hi));
+            }
+            __syncthreads();
+        }
         // unit u = (item, chunk) in item order goes to warp u mod kListWarps
         int u = 0;
         const int nit = i1 - i0;
@@ -182,7 +296,12 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
             if (c < nch) {
                 const int4 e = B.item[it];
                 for (; c < nch; c += kListWarps) {
-                    list_unit<R, REALH>(B, e, L.ent + r.x, r.y, c * kListChunk, lane, my);
+                    if constexpr (DF)
+                        list_unit_df<REALH>(reinterpret_cast<const float4 *>(B.row),
+                                            reinterpret_cast<const float4 *>(B.a), B.z, e, L.ent + r.x, r.y,
+                                            c * kListChunk, lane, reinterpret_cast<float4 *>(my));
+                    else
+                        list_unit<R, REALH>(B, e, L.ent + r.x, r.y, c * kListChunk, lane, my);
                     __syncwarp();
                 }
             }
@@ -197,11 +316,21 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
     ExpAcc<R> ea;
     for (int c = tid; c < dlo; c += kListThreads) {
         R sr = R(0), si = R(0);
+        if constexpr (DF) {
+            const float4 *acc4 = reinterpret_cast<const float4 *>(acc);
 #pragma unroll
-        for (int w = 0; w < kListWarps; ++w) {
-            const C2 a = acc[(size_t)w * dpad + c];
-            sr += a.x;
-            si += a.y;
+            for (int w = 0; w < kListWarps; ++w) {
+                const float4 a = acc4[(size_t)w * dpad + c];
+                sr += (double)a.x + (double)a.z;
+                si += (double)a.y + (double)a.w;
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < kListWarps; ++w) {
+                const C2 a = acc[(size_t)w * dpad + c];
+                sr += a.x;
+                si += a.y;
+            }
         }
         const int64_t idx = rc.own_base + c;
         if (flags & 1) {
@@ -239,13 +368,21 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
 
 template <typename R, bool REALH>
 void launch_list_k(const ApplyCfg &cfg, const SectorView &v, const Geom &geo, const PlanDev &pd, const ListDev &ld,
-                   const void *in, void *out, double *partials, int flags, cudaStream_t st) {
+                   const void *in, const float4 *in_df, void *out, double *partials, int flags, cudaStream_t st) {
     using C2 = typename Cx<R>::T;
-    auto kern = k_apply_list<R, REALH>;
-    smem_optin(reinterpret_cast<const void *>(kern), cfg.smem);
-    kern<<<(unsigned)cfg.nct, kListThreads, cfg.smem, st>>>(v, geo, pd, ld, static_cast<const C2 *>(in),
-                                                         static_cast<C2 *>(out), partials, flags);
-    PS_LAUNCH_CHECK();
+    auto run = [&](auto kern) {
+        smem_optin(reinterpret_cast<const void *>(kern), cfg.smem);
+        kern<<<(unsigned)cfg.nct, kListThreads, cfg.smem, st>>>(v, geo, pd, ld, static_cast<const C2 *>(in), in_df,
+                                                             static_cast<C2 *>(out), partials, flags);
+        PS_LAUNCH_CHECK();
+    };
+    if constexpr (sizeof(R) == 8) {
+        if (in_df) {
+            run(k_apply_list<R, REALH, true>);
+            return;
+        }
+    }
+    run(k_apply_list<R, REALH, false>);
 }
 
 template <typename R>
@@ -264,8 +401,20 @@ void launch_list_r(const ApplyCfg &cfg, const Plan &p, const ListTab &lt, const 
         kout = split_buf;
         flags = 1 | 4;
     }
-    if (p.real) launch_list_k<R, true>(cfg, v, geo, pd, ld, in, kout, partials, flags, st);
-    else launch_list_k<R, false>(cfg, v, geo, pd, ld, in, kout, partials, flags, st);
+    const float4 *in_df = nullptr;
+    if (sizeof(R) == 8) {
+        // complex128: split psi into hi / lo FP32 pairs once, into the plan's buffer
+        PS_CHECK(p.df_buf != nullptr && p.df_cap >= v.dim, PAULI_EINVAL,
+                 "apply: the plan's double-float buffer is missing (internal)");
+        if (v.dim > 0) {
+            k_split_df<<<(unsigned)((v.dim + 255) / 256), 256, 0, st>>>(static_cast<const double2 *>(in), p.df_buf,
+                                                                      v.dim);
+            PS_LAUNCH_CHECK();
+        }
+        in_df = p.df_buf;
+    }
+    if (p.real) launch_list_k<R, true>(cfg, v, geo, pd, ld, in, in_df, kout, partials, flags, st);
+    else launch_list_k<R, false>(cfg, v, geo, pd, ld, in, in_df, kout, partials, flags, st);
     if (cfg.nsplit > 1) {
         const int cflags = (out ? 1 : 0) | (partials ? 2 : 0);
         k_combine<R><<<(unsigned)cfg.combine_nct, kThreads, 0, st>>>(
@@ -371,6 +520,21 @@ void prepare_for_sector(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t
         }
         build_lists(H->al, p, v, st);
     }
+}
+
+void ensure_df_buffer(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t st) {
+    if (p.df_cap >= v.dim) return;
+    PS_CUDA(cudaStreamSynchronize(st));
+    dev_free(H->al, p.df_buf);
+    p.df_buf = nullptr;
+    p.df_cap = 0;
+    p.df_buf = static_cast<float4 *>(dev_alloc(H->al, (size_t)std::max<int64_t>(1, v.dim) * sizeof(float4)));
+    p.df_cap = v.dim;
+}
+
+void ensure_df_capacity(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t st) {
+    if (!find_lists(p, v.klo[0]) || !apply_config(p, v, PAULI_C128, true).list) return;
+    ensure_df_buffer(H, p, v, st);
 }
 
 void launch_list(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out, int dtype,

@@ -183,6 +183,9 @@ struct Plan {
     // partial vectors of split launches (bytes)
     void *split_buf = nullptr;
     int64_t split_cap = 0;
+    // complex128 list gather: psi split into hi / lo FP32 pairs (dim elements)
+    float4 *df_buf = nullptr;
+    int64_t df_cap = 0;
     // full-space passes over local bit sets (built on first use with a full sector)
     LocalPlan *local = nullptr;
     bool local_tried = false;
@@ -342,6 +345,10 @@ void free_lists(const Allocator &al, Plan &p);
 size_t list_smem(int dtype, int64_t dlo);
 void launch_list(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out, int dtype,
                  double *partials, void *split_buf, cudaStream_t st);
+// allocates the double-float copy of psi that the complex128 list gather reads,
+// when the plan's complex128 launch shape for this sector is the list gather
+void ensure_df_capacity(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t st);
+void ensure_df_buffer(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t st);  // unconditionally
 
 // local.cu
 LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st);

@@ -162,6 +162,12 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
         int64_t need = 0;
         for (const LaunchChoice &c : cand) need = std::max(need, apply_split_elems(p, v, dtype, &c) * (int64_t)es);
         ensure_split_capacity(H, p, need);
+        if (dtype == PAULI_C128)
+            for (const LaunchChoice &c : cand)
+                if (c.direct == 3) {
+                    ensure_df_buffer(H, p, v, cs);
+                    break;
+                }
         DevBuf<char> in(H->al, (size_t)v.dim * es), out(H->al, (size_t)v.dim * es);
         PS_CUDA(cudaMemsetAsync(in.p, 0x3c, (size_t)v.dim * es, cs));
         cudaEvent_t e0, e1;
@@ -235,6 +241,7 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
             const size_t es = dtype == PAULI_C64 ? 8 : 16;
             ensure_split_capacity(H, p, apply_split_elems(p, s->v, dtype, &c) * (int64_t)es);
             store_tuned(p, s->v, dtype, c, cfg->ms);
+            ensure_df_capacity(H, p, s->v, cs);
         } catch (...) {
             (void)cudaStreamDestroy(cs);
             throw;
