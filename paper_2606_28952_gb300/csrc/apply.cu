@@ -387,6 +387,24 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     c.nbuf = nbuf;
     c.smem = nbuf * bb + extra;
     c.base_nct = make_geom(v, tpt * kThreads).cta_off[v.nblk];
+    // SVD-factorised phases (installed or tuned; the plan must have been built for
+    // this sector's low half): one staged row per piece of groups sharing x_hi
+    if (ch.direct == 4 && svd_plan_fits(p.svd, v)) {
+        int t = ch.tpt == 2 || ch.tpt == 4 ? ch.tpt : 1;
+        c.svd = true;
+        c.ranked = true;
+        c.list = false;
+        c.tpt = t;
+        c.nbuf = 1;
+        c.smem = svd_smem(v, dtype);
+        c.base_nct = make_geom(v, t * kThreads).cta_off[v.nblk];
+        c.nsplit = 1;
+        c.split_p0.assign(2, 0);
+        c.split_p0[1] = (int32_t)p.P;
+        c.nct = c.base_nct;
+        c.combine_nct = 0;
+        return c;
+    }
     // full space with a local-pass plan (lattice operators, 2^21 amplitudes or more):
     // chunks staged in shared memory, one pass per local bit set
     if (v.kind == PAULI_SECTOR_FULL && p.local) {
@@ -500,6 +518,10 @@ void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *
     }
     if (cfg.list) {
         launch_list(cfg, p, v, psi_in, psi_out, dtype, partials, split_buf, st);
+        return;
+    }
+    if (cfg.svd) {
+        launch_svd(cfg, p, v, psi_in, psi_out, dtype, partials, st);
         return;
     }
     if (dtype == PAULI_C64) launch_apply_f32(cfg, p, v, psi_in, psi_out, partials, split_buf, st);

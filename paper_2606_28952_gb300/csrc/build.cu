@@ -503,6 +503,7 @@ void free_plan(const Allocator &al, Plan &p) {
     dev_free(al, p.partials);
     dev_free(al, p.split_buf);
     dev_free(al, p.df_buf);
+    free_svd_plan(p.svd);
     p = Plan();
 }
 

@@ -114,7 +114,8 @@ struct LaunchChoice {
     int nbuf = 0;     // staged source rows in flight: 1 or 2
     int nsplit = 0;   // piece ranges per row: 1..16
     int direct = -1;  // 1: direct gather (small plans), 0: staged, 2: local passes (full space),
-                      // 3: per-item lists of valid pairs (single block, n_lo <= kListMaxLo)
+                      // 3: per-item lists of valid pairs (single block, n_lo <= kListMaxLo),
+                      // 4: SVD-factorised phases (single block, real operator; svd.cu)
     int ranked = -1;  // 1: rows staged by rank + rank table, 0: by bit pattern
 };
 struct TunedEntry {
@@ -131,6 +132,7 @@ struct TunedEntry {
 //   item i    : one group, or a slice of a group's segments
 //   segment s : terms of one group with equal z_lo, sorted by (z_lo, z_hi)
 struct LocalPlan;  // local.cu
+struct SvdPlan;    // svd.cu
 
 // Lists of the valid (target, source) pairs of each distinct x_lo of a plan's
 // items in one single-block sector (low half of k_lo particles, n_lo <=
@@ -186,6 +188,8 @@ struct Plan {
     // complex128 list gather: psi split into hi / lo FP32 pairs (dim elements)
     float4 *df_buf = nullptr;
     int64_t df_cap = 0;
+    // SVD-factorised phases (built when that gather is installed or tuned)
+    SvdPlan *svd = nullptr;
     // full-space passes over local bit sets (built on first use with a full sector)
     LocalPlan *local = nullptr;
     bool local_tried = false;
@@ -312,6 +316,7 @@ struct ApplyCfg {
     bool local = false;     // full space: passes over local bit sets (local.cu)
     bool ranked = false;    // single block, rows staged by rank (KBLKR)
     bool list = false;      // single block, n_lo <= kListMaxLo: per-item lists of valid pairs (list.cu)
+    bool svd = false;       // single block, real operator: SVD-factorised phases (svd.cu)
 };
 ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_split,
                       const LaunchChoice *force = nullptr);
@@ -349,6 +354,16 @@ void launch_list(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const 
 // when the plan's complex128 launch shape for this sector is the list gather
 void ensure_df_capacity(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t st);
 void ensure_df_buffer(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t st);  // unconditionally
+
+// svd.cu
+SvdPlan *build_svd_plan(pauli_sum *H, const SectorView &v, cudaStream_t st);
+void free_svd_plan(SvdPlan *sp);
+bool svd_plan_fits(const SvdPlan *sp, const SectorView &v);  // built for this sector's low half
+size_t svd_smem(const SectorView &v, int dtype);
+int svd_batches(const SvdPlan *sp);
+const std::vector<int> &svd_rank_hist(const SvdPlan *sp);
+void launch_svd(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const void *in, void *out, int dtype,
+                double *partials, cudaStream_t st);
 
 // local.cu
 LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st);

@@ -44,7 +44,7 @@ pauli_launch_config to_public(const ApplyCfg &c, double ms) {
     o.cols_per_thread = c.tpt;
     o.staged_rows = c.nbuf;
     o.row_split = c.nsplit;
-    o.direct = c.list ? 3 : (c.local ? 2 : (c.direct ? 1 : 0));
+    o.direct = c.svd ? 4 : (c.list ? 3 : (c.local ? 2 : (c.direct ? 1 : 0)));
     o.ranked = c.ranked ? 1 : 0;
     o.ms = ms;
     return o;
@@ -129,6 +129,20 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
                 if (!cfg.list || cfg.nsplit != ns || cfg.smem > 226 * 1024) continue;
                 cand.push_back(c);
             }
+        if (v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1 && H->real) {
+            if (!svd_plan_fits(p.svd, v)) {
+                free_svd_plan(p.svd);
+                p.svd = nullptr;
+                p.svd = build_svd_plan(H, v, cs);
+            }
+            if (p.svd && svd_batches(p.svd) <= 4)
+                for (int tpt : {1, 2, 4}) {
+                    LaunchChoice c;
+                    c.tpt = tpt;
+                    c.direct = 4;
+                    if (apply_config(p, v, dtype, true, &c).svd && svd_smem(v, dtype) <= 226 * 1024) cand.push_back(c);
+                }
+        }
         for (int tpt : {1, 2, 4, 8}) {
             if (fits && tpt < 8) {
                 LaunchChoice c;
@@ -225,13 +239,23 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
                  PAULI_EINVAL, "cols_per_thread must be 1, 2, 4 or 8");
         PS_CHECK(cfg->staged_rows == 1 || cfg->staged_rows == 2, PAULI_EINVAL, "staged_rows must be 1 or 2");
         PS_CHECK(cfg->row_split >= 1 && cfg->row_split <= 16, PAULI_EINVAL, "row_split must be in 1..16");
-        PS_CHECK(cfg->direct >= 0 && cfg->direct <= 3, PAULI_EINVAL, "direct must be 0, 1, 2 or 3");
+        PS_CHECK(cfg->direct >= 0 && cfg->direct <= 4, PAULI_EINVAL, "direct must be 0, 1, 2, 3 or 4");
         PS_CHECK(cfg->ranked == 0 || cfg->ranked == 1, PAULI_EINVAL, "ranked must be 0 or 1");
         cudaStream_t cs = nullptr;
         PS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         try {
             Plan &p = get_plan(H, s->v, cs);
             prepare_for_sector(H, p, s->v, cs);
+            if (cfg->direct == 4) {
+                if (!svd_plan_fits(p.svd, s->v)) {
+                    free_svd_plan(p.svd);
+                    p.svd = nullptr;
+                    p.svd = build_svd_plan(H, s->v, cs);
+                }
+                PS_CHECK(p.svd != nullptr, PAULI_EUNSUPPORTED,
+                         "the SVD gather needs a real operator on a single product block with a low half of at "
+                         "most 16 qubits");
+            }
             LaunchChoice c;
             c.tpt = cfg->cols_per_thread;
             c.nbuf = cfg->staged_rows;
@@ -363,6 +387,43 @@ int pauli_tune_load(pauli_sum *H, const pauli_sector *s, const char *path, int *
             if (rc != PAULI_OK) return rc;
             ++*found;
         }
+        return PAULI_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PAULI_EINVAL;
+    }
+}
+
+int pauli_svd_ranks(pauli_sum *H, const pauli_sector *s, int *hist, int len, int *batches) {
+    try {
+        clear_error();
+        PS_CHECK(H && H->magic == kSumMagic, PAULI_EINVAL, "not a valid pauli_sum handle");
+        PS_CHECK(s && s->magic == kSectorMagic, PAULI_EINVAL, "not a valid pauli_sector handle");
+        PS_CHECK(H->n == s->v.n, PAULI_EINVAL, "operator and sector have different qubit counts");
+        PS_CHECK(hist != nullptr && len >= 1, PAULI_EINVAL, "hist is NULL or len < 1");
+        cudaStream_t cs = nullptr;
+        PS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        try {
+            Plan &p = get_plan(H, s->v, cs);
+            if (!svd_plan_fits(p.svd, s->v)) {
+                free_svd_plan(p.svd);
+                p.svd = nullptr;
+                p.svd = build_svd_plan(H, s->v, cs);
+            }
+            PS_CHECK(p.svd != nullptr, PAULI_EUNSUPPORTED,
+                     "the SVD factorisation needs a real operator on a single product block (low half <= 16 qubits)");
+            const std::vector<int> &h = svd_rank_hist(p.svd);
+            for (int i = 0; i < len; ++i) hist[i] = i < (int)h.size() ? h[i] : 0;
+            if (batches) *batches = svd_batches(p.svd);
+        } catch (...) {
+            (void)cudaStreamDestroy(cs);
+            throw;
+        }
+        PS_CUDA(cudaStreamSynchronize(cs));
+        (void)cudaStreamDestroy(cs);
         return PAULI_OK;
     } catch (const Error &e) {
         set_error(e.msg);
