@@ -55,7 +55,46 @@ void dev_free(const Allocator &a, void *p) {
     else (void)cudaFree(p);
 }
 
-void init_sector_view(SectorView &v, int n, int kind, int n_lo, int nb, const int *klo, const int *khi);
+void init_sector_view(SectorView &v, int n, int kind, int n_lo, int nb, const int *klo, const int *khi,
+                      const int *qubit_irrep = nullptr);
+
+// Raw entries of the operator product A B (eq. pauli_operator_multiplication,
+// eq. pauli_prod_x / pauli_prod_z / pauli_prod_phase), entry k * mb + l for
+// the pair (a_k, b_l):  x = xa ^ xb, z = za ^ zb,
+//   (X^xa Z^za)(X^xb Z^zb) = (-1)^popcount(za & xb) X^x Z^z,
+// so the XZ-form coefficient is Ca Cb (-1)^popcount(za & xb).  The complex
+// product is formed as (ar br - ai bi, ar bi + ai br) with separately rounded
+// products (no fused multiply-add); the sign is exact.
+__global__ void k_sum_product(int64_t ma, const uint64_t *__restrict__ xa, const uint64_t *__restrict__ za,
+                              const double2 *__restrict__ ca, int64_t mb, const uint64_t *__restrict__ xb,
+                              const uint64_t *__restrict__ zb, const double2 *__restrict__ cb, uint64_t *ox,
+                              uint64_t *oz, double2 *oc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ma * mb) return;
+    const int64_t k = i / mb, l = i - k * mb;
+    const uint64_t x1 = xa[k], z1 = za[k], x2 = xb[l], z2 = zb[l];
+    const double2 a = ca[k], b = cb[l];
+    const double rr = __dmul_rn(a.x, b.x), ii = __dmul_rn(a.y, b.y);
+    const double ri = __dmul_rn(a.x, b.y), ir = __dmul_rn(a.y, b.x);
+    double re = __dsub_rn(rr, ii), im = __dadd_rn(ri, ir);
+    if (__popcll(z1 & x2) & 1) {
+        re = -re;
+        im = -im;
+    }
+    ox[i] = x1 ^ x2;
+    oz[i] = z1 ^ z2;
+    oc[i] = make_double2(re, im);
+}
+
+// Raw entries of A + beta B: A's terms, then B's with beta C (same product rule).
+__global__ void k_sum_scaled_copy(int64_t m, const double2 *__restrict__ c, double br, double bi, double2 *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double2 a = c[i];
+    out[i] = make_double2(__dsub_rn(__dmul_rn(a.x, br), __dmul_rn(a.y, bi)),
+                          __dadd_rn(__dmul_rn(a.x, bi), __dmul_rn(a.y, br)));
+}
+
 
 namespace {
 std::mutex g_attr_mu;
@@ -219,6 +258,68 @@ Plan &ensure_plan(pauli_sum *H, const pauli_sector *s, cudaStream_t st, bool nee
 }  // namespace
 
 extern "C" {
+
+int pauli_sum_product(const pauli_sum *A, const pauli_sum *B, double eps_drop, pauli_sum **out) {
+    return guarded([&] {
+        PS_CHECK(out != nullptr, PAULI_EINVAL, "out is NULL");
+        *out = nullptr;
+        check_sum(A);
+        check_sum(B);
+        PS_CHECK(A->n == B->n, PAULI_EINVAL, "operands have different qubit counts");
+        PS_CHECK(std::isfinite(eps_drop) && eps_drop >= 0.0, PAULI_EINVAL, "eps_drop must be finite and >= 0");
+        const int64_t m = A->m * B->m;
+        PS_CHECK(A->m == 0 || m / A->m == B->m, PAULI_EUNSUPPORTED, "product too large");
+        PS_CHECK(m <= (1ll << 31), PAULI_EUNSUPPORTED,
+                 "product: more than 2^31 raw term pairs (" + std::to_string(m) + ")");
+        PrivateStream ps_;
+        SumGuard g(new_sum(A->n));
+        const Allocator &al = g.h->al;
+        DevBuf<uint64_t> dx(al, m), dz(al, m);
+        DevBuf<double2> dc(al, m);
+        if (m > 0) {
+            k_sum_product<<<(unsigned)((m + 255) / 256), 256, 0, ps_.s>>>(A->m, A->x, A->z, A->c, B->m, B->x, B->z,
+                                                                          B->c, dx.p, dz.p, dc.p);
+            PS_LAUNCH_CHECK();
+        }
+        canonicalize(g.h, m, dx.p, dz.p, dc.p, eps_drop, ps_.s);
+        PS_CUDA(cudaStreamSynchronize(ps_.s));
+        *out = g.release();
+    });
+}
+
+int pauli_sum_add(const pauli_sum *A, const pauli_sum *B, double beta_re, double beta_im, double eps_drop,
+                  pauli_sum **out) {
+    return guarded([&] {
+        PS_CHECK(out != nullptr, PAULI_EINVAL, "out is NULL");
+        *out = nullptr;
+        check_sum(A);
+        check_sum(B);
+        PS_CHECK(A->n == B->n, PAULI_EINVAL, "operands have different qubit counts");
+        PS_CHECK(std::isfinite(beta_re) && std::isfinite(beta_im), PAULI_EINVAL, "beta must be finite");
+        PS_CHECK(std::isfinite(eps_drop) && eps_drop >= 0.0, PAULI_EINVAL, "eps_drop must be finite and >= 0");
+        const int64_t m = A->m + B->m;
+        PrivateStream ps_;
+        SumGuard g(new_sum(A->n));
+        const Allocator &al = g.h->al;
+        DevBuf<uint64_t> dx(al, m), dz(al, m);
+        DevBuf<double2> dc(al, m);
+        if (A->m > 0) {
+            PS_CUDA(cudaMemcpyAsync(dx.p, A->x, A->m * 8, cudaMemcpyDeviceToDevice, ps_.s));
+            PS_CUDA(cudaMemcpyAsync(dz.p, A->z, A->m * 8, cudaMemcpyDeviceToDevice, ps_.s));
+            PS_CUDA(cudaMemcpyAsync(dc.p, A->c, A->m * 16, cudaMemcpyDeviceToDevice, ps_.s));
+        }
+        if (B->m > 0) {
+            PS_CUDA(cudaMemcpyAsync(dx.p + A->m, B->x, B->m * 8, cudaMemcpyDeviceToDevice, ps_.s));
+            PS_CUDA(cudaMemcpyAsync(dz.p + A->m, B->z, B->m * 8, cudaMemcpyDeviceToDevice, ps_.s));
+            k_sum_scaled_copy<<<(unsigned)((B->m + 255) / 256), 256, 0, ps_.s>>>(B->m, B->c, beta_re, beta_im,
+                                                                                dc.p + A->m);
+            PS_LAUNCH_CHECK();
+        }
+        canonicalize(g.h, m, dx.p, dz.p, dc.p, eps_drop, ps_.s);
+        PS_CUDA(cudaStreamSynchronize(ps_.s));
+        *out = g.release();
+    });
+}
 
 const char *pauli_last_error(void) { return g_err.c_str(); }
 
@@ -433,6 +534,48 @@ int pauli_sector_create(int n_qubits, int kind, int n_lo, int n_blocks, const in
         s->al = current_allocator();
         try {
             init_sector_view(s->v, n_qubits, kind, n_lo, n_blocks, k_lo, k_hi);
+            PrivateStream ps_;
+            build_sector_tables(s, ps_.s);
+        } catch (...) {
+            dev_free(s->al, s->tables);
+            delete s;
+            throw;
+        }
+        *out = s;
+    });
+}
+
+int pauli_sector_create_irrep(int n_qubits, int n_lo, int n_blocks, const int *k_lo, const int *irrep_lo,
+                              const int *k_hi, const int *irrep_hi, const int *qubit_irrep, pauli_sector **out) {
+    return guarded([&] {
+        PS_CHECK(out != nullptr, PAULI_EINVAL, "out is NULL");
+        *out = nullptr;
+        PS_CHECK(n_qubits >= 2 && n_qubits <= 2 * kMaxHalf, PAULI_EINVAL, "point-group sectors need 2 <= n_qubits <= 48");
+        PS_CHECK(n_lo >= 1 && n_lo < n_qubits && n_lo <= kMaxHalf && n_qubits - n_lo <= kMaxHalf, PAULI_EINVAL,
+                 "need 1 <= n_lo < n_qubits and both halves <= 24 qubits");
+        PS_CHECK(n_blocks >= 1 && n_blocks <= kMaxBlocks, PAULI_EINVAL, "need 1..33 blocks");
+        PS_CHECK(k_lo && k_hi && irrep_lo && irrep_hi && qubit_irrep, PAULI_EINVAL, "block / label arrays must not be NULL");
+        for (int q = 0; q < n_qubits; ++q)
+            PS_CHECK(qubit_irrep[q] >= 0 && qubit_irrep[q] <= 7, PAULI_EINVAL, "qubit irreps must be in 0..7");
+        std::vector<int> klo(n_blocks), khi(n_blocks);
+        bool seen[kMaxCls] = {};
+        for (int r = 0; r < n_blocks; ++r) {
+            PS_CHECK(k_lo[r] >= 0 && k_lo[r] <= n_lo && k_hi[r] >= 0 && k_hi[r] <= n_qubits - n_lo, PAULI_EINVAL,
+                     "k_lo / k_hi out of range");
+            PS_CHECK(irrep_lo[r] >= 0 && irrep_lo[r] <= 7 && irrep_hi[r] >= 0 && irrep_hi[r] <= 7, PAULI_EINVAL,
+                     "block irreps must be in 0..7");
+            klo[r] = k_lo[r] * 8 + irrep_lo[r];
+            khi[r] = k_hi[r] * 8 + irrep_hi[r];
+            PS_CHECK(!seen[khi[r]], PAULI_EINVAL, "the (k_hi, irrep_hi) of the blocks must be distinct");
+            seen[khi[r]] = true;
+        }
+        pauli_sector *s = new pauli_sector();
+        s->magic = kSectorMagic;
+        static std::atomic<uint64_t> next_uid{1ull << 40};
+        s->uid = next_uid.fetch_add(1);
+        s->al = current_allocator();
+        try {
+            init_sector_view(s->v, n_qubits, PAULI_SECTOR_BLOCKS, n_lo, n_blocks, klo.data(), khi.data(), qubit_irrep);
             PrivateStream ps_;
             build_sector_tables(s, ps_.s);
         } catch (...) {

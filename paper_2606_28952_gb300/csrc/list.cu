@@ -34,6 +34,10 @@ constexpr int kListThreads = 128;
 constexpr int kListWarps = kListThreads / 32;
 constexpr int kListK = 4;                     // list entries per lane in one unit
 constexpr int kListChunk = 32 * kListK;       // entries of one unit
+// the double-float path is latency-bound at two CTAs per SM (shared memory),
+// with registers to spare: twice the independent entries per lane
+constexpr int kListKDF = 8;
+constexpr int kListChunkDF = 32 * kListKDF;
 constexpr int kListTile = (int)kListMaxDlo;   // column tile of the geometry: a whole row
 
 struct ListDev {
@@ -179,19 +183,19 @@ __device__ __forceinline__ void list_unit_df(const float4 *__restrict__ row, con
                                              const uint32_t *__restrict__ zs, const int4 e,
                                              const uint32_t *__restrict__ ent, int len, int base, int lane,
                                              float4 *my) {
-    uint32_t w[kListK];
-    bool ok[kListK];
+    uint32_t w[kListKDF];
+    bool ok[kListKDF];
 #pragma unroll
-    for (int k = 0; k < kListK; ++k) {
+    for (int k = 0; k < kListKDF; ++k) {
         const int i = base + lane + 32 * k;
         ok[k] = i < len;
         w[k] = ok[k] ? __ldg(ent + i) : 0u;
     }
-    uint32_t s[kListK];
-    float4 amp[kListK];
-    float frh[kListK], frl[kListK], fih[kListK], fil[kListK];
+    uint32_t s[kListKDF];
+    float4 amp[kListKDF];
+    float frh[kListKDF], frl[kListKDF], fih[kListKDF], fil[kListKDF];
 #pragma unroll
-    for (int k = 0; k < kListK; ++k) {
+    for (int k = 0; k < kListKDF; ++k) {
         s[k] = (w[k] >> 20) ^ (uint32_t)e.x;
         amp[k] = row[(w[k] >> 10) & 1023u];
         frh[k] = frl[k] = fih[k] = fil[k] = 0.f;
@@ -202,7 +206,7 @@ __device__ __forceinline__ void list_unit_df(const float4 *__restrict__ row, con
         const uint32_t z = zs[sg];
         const float4 a = a4[sg];
 #pragma unroll
-        for (int k = 0; k < kListK; ++k) {
+        for (int k = 0; k < kListKDF; ++k) {
             const uint32_t par = __popc(z & s[k]);
             float t, err;
             two_sum(frh[k], flip(a.x, par), t, err);
@@ -216,7 +220,7 @@ __device__ __forceinline__ void list_unit_df(const float4 *__restrict__ row, con
         }
     }
 #pragma unroll
-    for (int k = 0; k < kListK; ++k) {
+    for (int k = 0; k < kListKDF; ++k) {
         if (!ok[k]) continue;
         float4 &o = my[w[k] & 1023u];
         float4 t = o;
@@ -288,9 +292,10 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
         // unit u = (item, chunk) in item order goes to warp u mod kListWarps
         int u = 0;
         const int nit = i1 - i0;
+        constexpr int kChunk = DF ? kListChunkDF : kListChunk;
         for (int it = 0; it < nit; ++it) {
             const int2 r = rng[it];
-            const int nch = (r.y + kListChunk - 1) / kListChunk;
+            const int nch = (r.y + kChunk - 1) / kChunk;
             int c = (warp - u) % kListWarps;
             if (c < 0) c += kListWarps;
             if (c < nch) {
@@ -299,7 +304,7 @@ k_apply_list(SectorView v, Geom geo, PlanDev p, ListDev L, const typename Cx<R>:
                     if constexpr (DF)
                         list_unit_df<REALH>(reinterpret_cast<const float4 *>(B.row),
                                             reinterpret_cast<const float4 *>(B.a), B.z, e, L.ent + r.x, r.y,
-                                            c * kListChunk, lane, reinterpret_cast<float4 *>(my));
+                                            c * kChunk, lane, reinterpret_cast<float4 *>(my));
                     else
                         list_unit<R, REALH>(B, e, L.ent + r.x, r.y, c * kListChunk, lane, my);
                     __syncwarp();
