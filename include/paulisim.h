@@ -132,6 +132,51 @@ int pauli_jw_fermion(int n_qubits, int n_terms, const int *n_factors, const int 
                      const int *daggers, const double *c_re, const double *c_im, double eps_drop,
                      pauli_sum **out);
 
+/* Canonical form of the operator product A B (eq. pauli_operator_multiplication:
+ * pairwise string products by eq. pauli_prod_x / pauli_prod_z /
+ * pauli_prod_phase).  In XZ form the product of terms a_k and b_l is
+ *   (Ca Cb (-1)^popcount(za & xb)) X^(xa ^ xb) Z^(za ^ zb);
+ * the raw entries in the order k * M_B + l (complex products with separately
+ * rounded parts, no fused multiply-add) are reduced as by pauli_sum_build.
+ * PAULI_EUNSUPPORTED beyond 2^31 raw pairs.  Blocking. */
+int pauli_sum_product(const pauli_sum *A, const pauli_sum *B, double eps_drop, pauli_sum **out);
+
+/* Canonical form of A + beta B (A's terms, then B's scaled by beta, reduced
+ * as by pauli_sum_build; e.g. beta = -1 for the commutator AB - BA of two
+ * products).  Blocking. */
+int pauli_sum_add(const pauli_sum *A, const pauli_sum *B, double beta_re, double beta_im, double eps_drop,
+                  pauli_sum **out);
+
+/* ------------------------------------------------------------------------- */
+/* Pauli sums on more than 64 qubits (multi-word masks; operator algebra only) */
+/* ------------------------------------------------------------------------- */
+
+/* The same canonical form for up to 256 qubits, with masks of
+ * W = ceil(n / 64) 64-bit words (word w holds qubits 64w .. 64w + 63; term t
+ * has words x[t * W + w], z[t * W + w]) and (x, z) ordered as unsigned
+ * multi-word integers, x first.  For the large Jordan-Wigner builds of
+ * Sec. 3.1.1; state-vector calls take the 64-qubit pauli_sum. */
+typedef struct pauli_wsum pauli_wsum;
+
+/* pauli_jw_fermion for n_qubits <= 256 (same arguments, raw order and reduction). */
+int pauli_wsum_jw_fermion(int n_qubits, int n_terms, const int *n_factors, const int *modes, const int *daggers,
+                          const double *c_re, const double *c_im, double eps_drop, pauli_wsum **out);
+
+/* pauli_jw_molecular for n_orb <= 128 (2 n_orb <= 256 qubits; same integral
+ * layout, skipping rules, raw order and reduction). */
+int pauli_wsum_jw_molecular(int n_orb, const double *h, const double *g, double e_nn, double eps_int,
+                            double eps_drop, pauli_wsum **out);
+
+/* pauli_sum_product for multi-word masks (PAULI_EUNSUPPORTED beyond 2^30 raw pairs). */
+int pauli_wsum_product(const pauli_wsum *A, const pauli_wsum *B, double eps_drop, pauli_wsum **out);
+
+int pauli_wsum_info(const pauli_wsum *h, int *n_qubits, int *words, int64_t *m, int64_t *n_groups);
+/* host arrays x, z of M * W words, c_re, c_im of M */
+int pauli_wsum_export(const pauli_wsum *h, uint64_t *x, uint64_t *z, double *c_re, double *c_im);
+/* group_start[G + 1]: term offsets of the X-mask groups */
+int pauli_wsum_groups(const pauli_wsum *h, int64_t *group_start);
+int pauli_wsum_destroy(pauli_wsum *h);
+
 /* Sizes: qubits, canonical terms M and X-mask groups G. */
 int pauli_sum_info(const pauli_sum *h, int *n_qubits, int64_t *m, int64_t *n_groups);
 
@@ -154,6 +199,21 @@ int pauli_sum_destroy(pauli_sum *h);
  * 0 <= k_lo <= n_lo, 0 <= k_hi <= n - n_lo and distinct k_hi.  Blocking. */
 int pauli_sector_create(int n_qubits, int kind, int n_lo, int n_blocks, const int *k_lo,
                         const int *k_hi, pauli_sector **out);
+
+/* A sector of abelian point-group blocks (Sec. 2.4: symmetry blocks r of
+ * eq. sreverse_sum).  qubit_irrep[q] (0..7, n_qubits entries) labels every
+ * qubit with an irrep of a group of order 8 whose product is XOR (e.g. D2h);
+ * the irrep of a half string is the XOR of its occupied qubits' labels.  Block
+ * r holds the configurations whose low n_lo qubits have k_lo[r] ones and
+ * irrep irrep_lo[r] and whose high qubits have k_hi[r] ones and irrep
+ * irrep_hi[r]; the (k_hi, irrep_hi) of the blocks must be distinct.  Inside a
+ * block index = off_r + rank(b_hi) D_lo^r + rank(b_lo), rank = position in
+ * ascending numeric order among the strings of the same (popcount, irrep).
+ * Every apply / expect / rotate / pool / Krylov call takes these sectors;
+ * pair-listed rotations and the rank-staged gathers of low halves wider than
+ * 14 qubits fall back to the per-target kernels.  Blocking. */
+int pauli_sector_create_irrep(int n_qubits, int n_lo, int n_blocks, const int *k_lo, const int *irrep_lo,
+                              const int *k_hi, const int *irrep_hi, const int *qubit_irrep, pauli_sector **out);
 
 int pauli_sector_dim(const pauli_sector *s, int64_t *dim);
 
@@ -386,7 +446,9 @@ typedef struct {
     int row_split;        /* 1..16 */
     int direct;           /* 0 staged rows, 1 direct gather (small operators),
                              2 full space in passes over local bit sets (lattice operators),
-                             3 lists of valid pairs (single block, low half <= 12 qubits) */
+                             3 lists of valid pairs (single block, low half <= 12 qubits),
+                             4 SVD-factorised phases (real operator, single block; see
+                               pauli_svd_ranks) */
     int ranked;           /* 0 or 1 */
     double ms;
 } pauli_launch_config;
@@ -402,6 +464,23 @@ int pauli_set_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, cons
 
 /* The shape pauli_apply currently uses for this sector and dtype (needs a plan). */
 int pauli_get_launch_config(pauli_sum *H, const pauli_sector *s, int dtype, pauli_launch_config *cfg);
+
+/* The gather of eq. svd_sreverse_sum (Sec. 2.4, Algorithm 2), installed with
+ * direct = 4 (cols_per_thread 1, 2 or 4) or chosen by pauli_tune: for every
+ * X-mask group the matrix M_{mu nu} of its coefficients over its distinct
+ * (low, high) Z-mask pairs is factorised by SVD (one-sided Jacobi, FP64,
+ * singular values above 1e-12 kept), M = sum_k Wa_k Wb_k^T, so that its phase
+ * sum at a target is sum_k Fa(t_lo, k) Fb(t_hi, k).  Fb is evaluated once per
+ * (row, group) and Fa is tabulated for the low half in on-the-fly batches of
+ * groups (at most 256 MB of table at a time); a batch after the first adds to
+ * the output, so an expectation without hpsi_out on an operator that needs
+ * several batches returns PAULI_EUNSUPPORTED.  Needs a real operator on a
+ * single product block with a low half of at most 16 qubits
+ * (PAULI_EUNSUPPORTED otherwise).  pauli_svd_ranks builds the factorisation
+ * if needed (blocking) and reports hist[R] = number of groups of rank R
+ * (R < len; groups whose coefficients all cancel have rank 0) and the number
+ * of on-the-fly batches. */
+int pauli_svd_ranks(pauli_sum *H, const pauli_sector *s, int *hist, int len, int *batches);
 
 /* Cache of tuned shapes in a text file (one line per (operator, sector,
  * dtype): a tag, a key, the dtype and the five fields and ms of

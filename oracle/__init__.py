@@ -69,6 +69,8 @@ def lib():
         L.orc_canonical.restype = C.c_int64
         L.orc_sector_new.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _i32p, _i32p]
         L.orc_sector_new.restype = C.c_void_p
+        L.orc_sector_new_irrep.argtypes = [C.c_int, C.c_int, C.c_int, _i32p, _i32p, _i32p, _i32p, _i32p]
+        L.orc_sector_new_irrep.restype = C.c_void_p
         L.orc_sector_free.argtypes = [C.c_void_p]
         L.orc_sector_dim.argtypes = [C.c_void_p]
         L.orc_sector_dim.restype = C.c_int64
@@ -251,6 +253,17 @@ class Sector:
         klo = np.array([b[0] for b in self.blocks] or [0], dtype=np.int32)
         khi = np.array([b[1] for b in self.blocks] or [0], dtype=np.int32)
         self._h = lib().orc_sector_new(n, kind, n_lo, len(self.blocks), klo, khi)
+
+    @classmethod
+    def irrep_blocks(cls, n: int, n_lo: int, blocks, qubit_irrep):
+        """Point-group blocks (k_lo, irrep_lo, k_hi, irrep_hi); qubit_irrep[q] in 0..7."""
+        self = cls.__new__(cls)
+        self.n, self.kind, self.n_lo = n, BLOCKS, n_lo
+        self.blocks = [tuple(b) for b in blocks]
+        arr = lambda i: np.array([b[i] for b in self.blocks] or [0], dtype=np.int32)
+        qi = np.ascontiguousarray(np.asarray(qubit_irrep, dtype=np.int32))
+        self._h = lib().orc_sector_new_irrep(n, n_lo, len(self.blocks), arr(0), arr(2), arr(1), arr(3), qi)
+        return self
 
     @classmethod
     def full(cls, n):

@@ -406,7 +406,21 @@ typedef struct {
     int64_t *blk_off;    /* nblk + 1 */
     int *klo, *khi;
     int32_t *inv;        /* configuration -> index, or -1 (n <= 28 only) */
+    int irr;             /* 1: blocks also fix the point-group irrep of each half */
+    int *irlo, *irhi;    /* irrep label of each block's low / high half */
+    int qirr[64];        /* irrep label (0..7) of every qubit */
 } orc_sector;
+
+/* Irrep of a string of `bits` qubits starting at qubit `first`: the product
+ * (XOR of the labels) of the irreps of its occupied orbitals (abelian point
+ * group with 2^3 irreps, e.g. D2h). */
+static int string_irrep(const orc_sector *s, uint64_t v, int first, int bits)
+{
+    int g = 0;
+    for (int j = 0; j < bits; ++j)
+        if ((v >> j) & 1u) g ^= s->qirr[first + j];
+    return g;
+}
 
 static int64_t popc_count_list(int bits, int k, uint64_t *out)
 {
@@ -484,7 +498,56 @@ void orc_sector_free(orc_sector *s)
 {
     if (!s) return;
     free(s->cfg); free(s->blk_off); free(s->klo); free(s->khi); free(s->inv);
+    free(s->irlo); free(s->irhi);
     free(s);
+}
+
+/* A sector of point-group blocks r = (k_lo, irrep_lo, k_hi, irrep_hi): the
+ * configurations whose low half holds k_lo ones with irrep irrep_lo and whose
+ * high half holds k_hi ones with irrep irrep_hi (qubit q has irrep
+ * qubit_irrep[q]); inside a block ascending numeric order, high part slowest;
+ * blocks in the order given. */
+orc_sector *orc_sector_new_irrep(int n, int n_lo, int nblk, const int *klo, const int *khi, const int *irlo,
+                                 const int *irhi, const int *qubit_irrep)
+{
+    orc_sector *s = (orc_sector *)calloc(1, sizeof(orc_sector));
+    s->n = n; s->kind = 1; s->n_lo = n_lo; s->nblk = nblk; s->irr = 1;
+    for (int q = 0; q < n && q < 64; ++q) s->qirr[q] = qubit_irrep[q];
+    s->blk_off = (int64_t *)calloc((size_t)(nblk + 1), sizeof(int64_t));
+    s->klo = (int *)calloc((size_t)(nblk > 0 ? nblk : 1), sizeof(int));
+    s->khi = (int *)calloc((size_t)(nblk > 0 ? nblk : 1), sizeof(int));
+    s->irlo = (int *)calloc((size_t)(nblk > 0 ? nblk : 1), sizeof(int));
+    s->irhi = (int *)calloc((size_t)(nblk > 0 ? nblk : 1), sizeof(int));
+    int n_hi = n - n_lo;
+    uint64_t nlo = ((uint64_t)1) << n_lo, nhi = ((uint64_t)1) << n_hi;
+    int64_t total = 0;
+    for (int r = 0; r < nblk; ++r) {
+        s->klo[r] = klo[r]; s->khi[r] = khi[r]; s->irlo[r] = irlo[r]; s->irhi[r] = irhi[r];
+        int64_t a = 0, b = 0;
+        for (uint64_t v = 0; v < nlo; ++v)
+            if (popc64(v) == klo[r] && string_irrep(s, v, 0, n_lo) == irlo[r]) ++a;
+        for (uint64_t v = 0; v < nhi; ++v)
+            if (popc64(v) == khi[r] && string_irrep(s, v, n_lo, n_hi) == irhi[r]) ++b;
+        s->blk_off[r] = total;
+        total += a * b;
+    }
+    s->blk_off[nblk] = total;
+    s->dim = total;
+    s->cfg = (uint64_t *)malloc((size_t)(total > 0 ? total : 1) * sizeof(uint64_t));
+    int64_t p = 0;
+    for (int r = 0; r < nblk; ++r)
+        for (uint64_t hv = 0; hv < nhi; ++hv) {
+            if (popc64(hv) != khi[r] || string_irrep(s, hv, n_lo, n_hi) != irhi[r]) continue;
+            for (uint64_t lv = 0; lv < nlo; ++lv)
+                if (popc64(lv) == klo[r] && string_irrep(s, lv, 0, n_lo) == irlo[r]) s->cfg[p++] = lv | (hv << n_lo);
+        }
+    if (n <= 28) {
+        int64_t full = ((int64_t)1) << n;
+        s->inv = (int32_t *)malloc((size_t)full * sizeof(int32_t));
+        for (int64_t v = 0; v < full; ++v) s->inv[v] = -1;
+        for (int64_t i = 0; i < s->dim; ++i) s->inv[s->cfg[i]] = (int32_t)i;
+    }
+    return s;
 }
 
 int64_t orc_sector_dim(const orc_sector *s) { return s->dim; }
@@ -506,6 +569,9 @@ int64_t orc_sector_index(const orc_sector *s, uint64_t b)
     int kl = popc64(b & lomask), kh = popc64(b >> s->n_lo);
     for (int r = 0; r < s->nblk; ++r) {
         if (s->klo[r] != kl || s->khi[r] != kh) continue;
+        if (s->irr && (string_irrep(s, b & lomask, 0, s->n_lo) != s->irlo[r] ||
+                       string_irrep(s, b >> s->n_lo, s->n_lo, s->n - s->n_lo) != s->irhi[r]))
+            continue;
         int64_t lo = s->blk_off[r], hi = s->blk_off[r + 1] - 1;
         while (lo <= hi) {
             int64_t mid = lo + (hi - lo) / 2;

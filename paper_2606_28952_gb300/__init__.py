@@ -44,11 +44,21 @@ SIGNATURES = {
     "pauli_jw_molecular": (_i32, [_i32, _vp, _vp, _dbl, _dbl, _dbl, _vp]),
     "pauli_jw_molecular_raw": (_i32, [_i32, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp, _vp, _vp]),
     "pauli_jw_fermion": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _dbl, _vp]),
+    "pauli_sum_product": (_i32, [_vp, _vp, _dbl, _vp]),
+    "pauli_sum_add": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _vp]),
     "pauli_sum_info": (_i32, [_vp, _vp, _vp, _vp]),
+    "pauli_wsum_jw_fermion": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _dbl, _vp]),
+    "pauli_wsum_jw_molecular": (_i32, [_i32, _vp, _vp, _dbl, _dbl, _dbl, _vp]),
+    "pauli_wsum_product": (_i32, [_vp, _vp, _dbl, _vp]),
+    "pauli_wsum_info": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "pauli_wsum_export": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "pauli_wsum_groups": (_i32, [_vp, _vp]),
+    "pauli_wsum_destroy": (_i32, [_vp]),
     "pauli_sum_export": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "pauli_sum_groups": (_i32, [_vp, _vp, _vp]),
     "pauli_sum_destroy": (_i32, [_vp]),
     "pauli_sector_create": (_i32, [_i32, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "pauli_sector_create_irrep": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pauli_sector_dim": (_i32, [_vp, _vp]),
     "pauli_sector_rank": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "pauli_sector_unrank": (_i32, [_vp, _vp, _i64, _vp, _vp]),
@@ -75,6 +85,7 @@ SIGNATURES = {
     "pauli_set_launch_config": (_i32, [_vp, _vp, _i32, _vp]),
     "pauli_get_launch_config": (_i32, [_vp, _vp, _i32, _vp]),
     "pauli_tune_save": (_i32, [_vp, _vp, C.c_char_p]),
+    "pauli_svd_ranks": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "pauli_tune_load": (_i32, [_vp, _vp, C.c_char_p, _vp]),
     "pauli_batch_create": (_i32, [_i32, _vp, _vp, _i32, _vp]),
     "pauli_batch_apply": (_i32, [_vp, _vp, _vp, _vp, _vp]),
@@ -190,6 +201,27 @@ class PauliSum:
                                       _np_ptr(cim), eps_drop, C.byref(out)))
         return cls(out.value)
 
+    # -- algebra --------------------------------------------------------------
+    def __matmul__(self, other: "PauliSum") -> "PauliSum":
+        """Canonical operator product self @ other (pauli_sum_product)."""
+        return self.product(other)
+
+    def product(self, other: "PauliSum", eps_drop: float = 0.0) -> "PauliSum":
+        out = C.c_void_p()
+        _check(lib().pauli_sum_product(self._h, other._h, eps_drop, C.byref(out)))
+        return PauliSum(out.value)
+
+    def add(self, other: "PauliSum", beta: complex = 1.0, eps_drop: float = 0.0) -> "PauliSum":
+        """Canonical self + beta * other (pauli_sum_add)."""
+        out = C.c_void_p()
+        b = complex(beta)
+        _check(lib().pauli_sum_add(self._h, other._h, b.real, b.imag, eps_drop, C.byref(out)))
+        return PauliSum(out.value)
+
+    def commutator(self, other: "PauliSum", eps_drop: float = 0.0) -> "PauliSum":
+        """[self, other] = self other - other self, canonical."""
+        return self.product(other).add(other.product(self), -1.0, eps_drop)
+
     # -- properties ---------------------------------------------------------
     def info(self):
         n, m, g = C.c_int(), C.c_int64(), C.c_int64()
@@ -243,6 +275,80 @@ class PauliSum:
             pass
 
 
+class WidePauliSum:
+    """Canonical Pauli sum with multi-word masks (up to 256 qubits): the
+    operator algebra of large Jordan-Wigner builds (pauli_wsum_*).  export()
+    gives the masks as Python integers."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+
+    @classmethod
+    def jw_fermion(cls, n: int, terms, eps_drop: float = 0.0):
+        nf = np.array([len(f) for _, f in terms], np.int32)
+        modes = np.array([m for _, f in terms for m, _ in f] or [0], np.int32)
+        dag = np.array([int(d) for _, f in terms for _, d in f] or [0], np.int32)
+        cre = np.array([complex(c).real for c, _ in terms] or [0.0], np.float64)
+        cim = np.array([complex(c).imag for c, _ in terms] or [0.0], np.float64)
+        out = C.c_void_p()
+        _check(lib().pauli_wsum_jw_fermion(n, len(terms), _np_ptr(nf), _np_ptr(modes), _np_ptr(dag), _np_ptr(cre),
+                                           _np_ptr(cim), eps_drop, C.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def jw_molecular(cls, h, g, e_nn: float = 0.0, eps_int: float = 0.0, eps_drop: float = 0.0):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        out = C.c_void_p()
+        _check(lib().pauli_wsum_jw_molecular(h.shape[0], _np_ptr(h), _np_ptr(g), e_nn, eps_int, eps_drop,
+                                             C.byref(out)))
+        return cls(out.value)
+
+    def __matmul__(self, other: "WidePauliSum") -> "WidePauliSum":
+        out = C.c_void_p()
+        _check(lib().pauli_wsum_product(self._h, other._h, 0.0, C.byref(out)))
+        return WidePauliSum(out.value)
+
+    def info(self):
+        n, wds, m, g = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+        _check(lib().pauli_wsum_info(self._h, C.byref(n), C.byref(wds), C.byref(m), C.byref(g)))
+        return n.value, wds.value, m.value, g.value
+
+    @property
+    def m(self) -> int:
+        return self.info()[2]
+
+    def export(self):
+        """(x, z, C): lists of Python-int masks and a complex128 array (XZ form)."""
+        n, W, m, _ = self.info()
+        xw = np.zeros(max(m * W, 1), np.uint64)
+        zw = np.zeros(max(m * W, 1), np.uint64)
+        re = np.zeros(max(m, 1))
+        im = np.zeros(max(m, 1))
+        _check(lib().pauli_wsum_export(self._h, _np_ptr(xw), _np_ptr(zw), _np_ptr(re), _np_ptr(im)))
+        def words(a, t):
+            return sum(int(a[t * W + k]) << (64 * k) for k in range(W))
+        return [words(xw, t) for t in range(m)], [words(zw, t) for t in range(m)], re[:m] + 1j * im[:m]
+
+    def groups(self):
+        _, _, _, g = self.info()
+        gs = np.zeros(g + 1, np.int64)
+        _check(lib().pauli_wsum_groups(self._h, _np_ptr(gs)))
+        return gs
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            if _lib is not None:
+                lib().pauli_wsum_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def jw_molecular_raw(h, g, e_nn: float = 0.0, eps_int: float = 0.0):
     """Raw (pre-reduction) Jordan-Wigner entries (x, z, C) as numpy arrays."""
     h = np.ascontiguousarray(h, dtype=np.float64)
@@ -276,6 +382,26 @@ class Sector:
         d = C.c_int64()
         _check(lib().pauli_sector_dim(self._h, C.byref(d)))
         self.dim = d.value
+
+    @classmethod
+    def irrep_blocks(cls, n: int, n_lo: int, blocks, qubit_irrep):
+        """Point-group blocks (k_lo, irrep_lo, k_hi, irrep_hi) with per-qubit irrep
+        labels 0..7 (pauli_sector_create_irrep)."""
+        self = cls.__new__(cls)
+        blocks = [tuple(int(v) for v in b) for b in blocks]
+        arr = lambda i: np.array([b[i] for b in blocks] or [0], np.int32)
+        qi = np.ascontiguousarray(np.asarray(qubit_irrep, dtype=np.int32))
+        if qi.size != n:
+            raise ValueError("qubit_irrep needs one label per qubit")
+        out = C.c_void_p()
+        _check(lib().pauli_sector_create_irrep(n, n_lo, len(blocks), _np_ptr(arr(0)), _np_ptr(arr(1)), _np_ptr(arr(2)),
+                                               _np_ptr(arr(3)), _np_ptr(qi), C.byref(out)))
+        self._h = out
+        self.n, self.kind, self.n_lo, self.blocks = n, BLOCKS, n_lo, blocks
+        d = C.c_int64()
+        _check(lib().pauli_sector_dim(self._h, C.byref(d)))
+        self.dim = d.value
+        return self
 
     @classmethod
     def full(cls, n: int, n_lo: int = 0):
@@ -394,6 +520,15 @@ def tune(H: PauliSum, s: Sector, dtype=None, reps: int = 5, cache: str | None = 
     if cache:
         _check(lib().pauli_tune_save(H._h, s._h, os.fsencode(cache)))
     return dict(cfg.as_dict(), cached=False)
+
+
+def svd_ranks(H: PauliSum, s: Sector, max_rank: int = 65):
+    """(hist, batches): hist[R] = number of X-mask groups whose coefficient matrix
+    has SVD rank R (pauli_svd_ranks), and the gather's on-the-fly batch count."""
+    hist = np.zeros(max_rank, np.int32)
+    nb = C.c_int(0)
+    _check(lib().pauli_svd_ranks(H._h, s._h, _np_ptr(hist), max_rank, C.byref(nb)))
+    return hist, nb.value
 
 
 def set_launch_config(H: PauliSum, s: Sector, dtype, cfg: "LaunchConfig"):

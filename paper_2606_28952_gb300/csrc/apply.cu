@@ -79,8 +79,8 @@ k_rotate(SectorView v, Geom geo, int64_t m, uint64_t x, const uint64_t *__restri
     if (FULL) {
         sidx = (int64_t)s;
     } else {
-        const int bb = v.blk_of_khi[__popc(shi)];
-        if (bb < 0 || __popc(slo) != v.klo[bb]) {
+        const int bb = v.blk_of_khi[cls_hi(v, shi)];
+        if (bb < 0 || cls_lo(v, slo) != v.klo[bb]) {
             if (fr != R(0) || fi != R(0)) atomicCAS(status, 0, (int)PAULI_ESECTOR);
             return;
         }
@@ -171,8 +171,8 @@ k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const
         if (FULL) {
             sidx = (int64_t)s;
         } else {
-            const int bb = v.blk_of_khi[__popc(shi)];
-            if (bb < 0 || __popc(slo) != v.klo[bb]) {
+            const int bb = v.blk_of_khi[cls_hi(v, shi)];
+            if (bb < 0 || cls_lo(v, slo) != v.klo[bb]) {
                 if (fr != R(0) || fi != R(0)) atomicCAS(status, 0, (int)PAULI_ESECTOR);
                 continue;
             }
@@ -366,7 +366,7 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     // be staged densely by rank (D_lo slots) plus a rank table
     const bool single = v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1;
     const size_t bb_pattern = buf_bytes(1 << v.n_lo);
-    const bool rank_ok = single && v.n_lo <= 16;
+    const bool rank_ok = single && v.n_lo <= (v.irr ? 14 : 16);
     const int dflt_ranked = (single && bb_pattern > kMaxDynSmem) ? 1 : 0;
     c.ranked = rank_ok && (ch.ranked >= 0 ? ch.ranked != 0 : dflt_ranked != 0);
     const size_t bb = c.ranked ? buf_bytes(ranked_rowcap(v.dlo[0])) : bb_pattern;
@@ -619,7 +619,7 @@ static bool rotation_leaks(pauli_sum *G, const SectorView &v, uint64_t x, cudaSt
 // that leaks out of the sector (its leaks are then recorded on every call).
 const RotPairs *rotation_pairs(pauli_sum *G, const pauli_sector *sec, uint64_t x, cudaStream_t st) {
     const SectorView &v = sec->v;
-    if (v.kind != PAULI_SECTOR_BLOCKS || v.nblk != 1 || x == 0 || G->m > kRotPairTerms) return nullptr;
+    if (v.kind != PAULI_SECTOR_BLOCKS || v.nblk != 1 || v.irr || x == 0 || G->m > kRotPairTerms) return nullptr;
     for (int i = 0; i < G->nrot; ++i)
         if (G->rot[i].sector_uid == sec->uid) return G->rot[i].leaks ? nullptr : &G->rot[i];
     RotPairs rp;

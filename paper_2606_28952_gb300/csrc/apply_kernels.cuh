@@ -278,7 +278,7 @@ __device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &
         base = (int64_t)shi << v.n_lo;
         len = 1ll << v.n_lo;
     } else {
-        const int bb = v.blk_of_khi[__popc(shi)];
+        const int bb = v.blk_of_khi[cls_hi(v, shi)];
         klo = v.klo[bb];
         base = v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
         len = v.dlo[bb];
@@ -353,7 +353,7 @@ __device__ __forceinline__ int next_piece(const SectorView &v, const PlanDev &p,
     for (++q; q < pend; ++q) {
         if (KIND == KFULL) break;
         const uint32_t shi = thi ^ __ldg(p.pc_xhi + q);
-        if (v.blk_of_khi[__popc(shi)] >= 0) break;
+        if (v.blk_of_khi[cls_hi(v, shi)] >= 0) break;
     }
     return q;
 }
@@ -374,7 +374,7 @@ __device__ __forceinline__ uint32_t ranked_index(const RankTab &rt, uint32_t s) 
 }
 
 template <typename R, int KIND, bool REALH, int TPT>
-__device__ __forceinline__ void gather_piece(const PlanDev &p, int q, const Buf<R> &B, int klo_req,
+__device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev &p, int q, const Buf<R> &B, int klo_req,
                                              const uint32_t (&tlo)[TPT], R (&accr)[TPT], R (&acci)[TPT],
                                              const RankTab &rt) {
     using C2 = typename Cx<R>::T;
@@ -442,7 +442,7 @@ __device__ __forceinline__ void gather_piece(const PlanDev &p, int q, const Buf<
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
             C2 amp = amp0[j];
-            if (KIND == KBLKN && __popc(s[j]) != klo_req) {
+            if (KIND == KBLKN && cls_lo(v, s[j]) != klo_req) {
                 amp.x = R(0);
                 amp.y = R(0);
             }
@@ -473,7 +473,7 @@ __device__ __forceinline__ void lofree_piece(const SectorView &v, const PlanDev 
     if (KIND == KFULL) {
         base = (int64_t)shi << v.n_lo;
     } else {
-        const int bb = v.blk_of_khi[__popc(shi)];
+        const int bb = v.blk_of_khi[cls_hi(v, shi)];
         base = v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
     }
     C2 amp[TPT];
@@ -548,7 +548,7 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
         if (v.n_lo <= 14) {
             uint16_t *lut = reinterpret_cast<uint16_t *>(tab);
             for (int s = tid; s < (1 << v.n_lo); s += kThreads)
-                lut[s] = (uint16_t)(__popc(s) == klo ? __ldg(v.rank_lo + s) : (uint32_t)dlo);
+                lut[s] = (uint16_t)(cls_lo(v, (uint32_t)s) == klo ? __ldg(v.rank_lo + s) : (uint32_t)dlo);
         } else {
             uint32_t *tabA = reinterpret_cast<uint32_t *>(tab);
             uint32_t *tabB = tabA + 256;
@@ -604,7 +604,7 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
                 cp_async_wait<0>();
             }
             __syncthreads();
-            gather_piece<R, KIND, REALH, TPT>(p, q, c ? B1 : B0, klo_req[c], tlo, accr, acci, rt);
+            gather_piece<R, KIND, REALH, TPT>(v, p, q, c ? B1 : B0, klo_req[c], tlo, accr, acci, rt);
             __syncthreads();
             c ^= 1;
             q = qn;
@@ -617,7 +617,7 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
                 stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
                 cp_async_wait<0>();
                 __syncthreads();
-                gather_piece<R, KIND, REALH, TPT>(p, q, B0, klo_req[0], tlo, accr, acci, rt);
+                gather_piece<R, KIND, REALH, TPT>(v, p, q, B0, klo_req[0], tlo, accr, acci, rt);
                 __syncthreads();
             }
             q = next_piece<R, KIND>(v, p, q, rc.thi, pend);
@@ -802,7 +802,7 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
             e.klo = 0;
             e.base = (int64_t)shi << v.n_lo;
         } else {
-            const int bb = v.blk_of_khi[__popc(shi)];
+            const int bb = v.blk_of_khi[cls_hi(v, shi)];
             e.klo = bb < 0 ? -1 : v.klo[bb];
             e.base = bb < 0 ? 0 : v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
         }
@@ -884,7 +884,7 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
                 s[j] = tlo[j] ^ e.xlo;
-                const bool ok = act[j] && (__popc(s[j]) == e.klo);
+                const bool ok = act[j] && (cls_lo(v, s[j]) == e.klo);
                 const int64_t idx = e.base + (ok ? (int64_t)__ldg(v.rank_lo + s[j]) : 0);
                 amp[j] = psi[idx];
                 if (!ok) {

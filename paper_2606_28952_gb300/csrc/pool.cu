@@ -171,8 +171,8 @@ k_pool_generic(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, con
         if (FULL) {
             sidx = (int64_t)s;
         } else {
-            const int bb = v.blk_of_khi[__popc(shi)];
-            if (bb < 0 || __popc(slo) != v.klo[bb]) {
+            const int bb = v.blk_of_khi[cls_hi(v, shi)];
+            if (bb < 0 || cls_lo(v, slo) != v.klo[bb]) {
                 // P_S G P_S: a source outside the sector contributes nothing; record the leak
                 if (fr != R(0) || fi != R(0)) atomicCAS(status, 0, (int)PAULI_ESECTOR);
                 continue;

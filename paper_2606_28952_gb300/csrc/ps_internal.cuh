@@ -85,24 +85,55 @@ struct DevBuf {
 // ---------------------------------------------------------------------------
 constexpr int kMaxBlocks = 33;
 constexpr int kMaxHalf = 24;  // largest half width with rank / unrank tables
+constexpr int kMaxCls = (kMaxHalf + 1) * 8;  // half-string classes (see SectorView)
 
 // Everything a kernel needs to know about a sector, passed by value.
+//
+// The class of a half string (its low or high half of the qubits) is its
+// popcount, or, in a sector with point-group labels (irr = 1), popcount * 8 +
+// irrep, the irrep being the XOR of the labels (0..7) of its occupied qubits:
+// bit j of it is the parity of popcount(s & irr_lo[j]) (irr_hi[j] for the high
+// half).  A block r is the product of the low strings of class klo[r] and the
+// high strings of class khi[r]; the khi of the blocks are distinct.  Inside a
+// class the strings are ranked in ascending numeric order (colex rank for
+// popcount classes).
 struct SectorView {
     int n, n_lo, n_hi, kind, nblk;
+    int irr;                          // 1: classes carry a point-group irrep
+    uint32_t irr_lo[3], irr_hi[3];    // irrep-bit masks of the two halves
     int64_t dim;
     int64_t nrows;                    // sum over blocks of D_hi
-    int klo[kMaxBlocks], khi[kMaxBlocks];
+    int klo[kMaxBlocks], khi[kMaxBlocks];  // class of each block's low / high half
     int64_t off[kMaxBlocks + 1];      // first index of each block
     int64_t dlo[kMaxBlocks], dhi[kMaxBlocks];
     int64_t row_off[kMaxBlocks + 1];  // first row of each block
-    int blk_of_khi[kMaxHalf + 9];     // k_hi -> block or -1 (size n_hi + 1 used)
-    const uint32_t *rank_lo;          // [2^n_lo] colex rank among equal popcount
+    int blk_of_khi[kMaxCls];          // class of the high half -> block or -1
+    const uint32_t *rank_lo;          // [2^n_lo] rank inside the string's class
     const uint32_t *rank_hi;          // [2^n_hi]
-    const uint32_t *list_lo;          // [2^n_lo] strings ordered by (popcount, value)
+    const uint32_t *list_lo;          // [2^n_lo] strings ordered by (class, value)
     const uint32_t *list_hi;          // [2^n_hi]
-    int64_t list_lo_off[kMaxHalf + 2];  // first entry of each popcount in list_lo
-    int64_t list_hi_off[kMaxHalf + 2];
+    int64_t list_lo_off[kMaxCls + 1];  // first entry of each class in list_lo
+    int64_t list_hi_off[kMaxCls + 1];
 };
+
+__host__ __device__ __forceinline__ int ps_popc32(uint32_t v) {
+#ifdef __CUDA_ARCH__
+    return __popc(v);
+#else
+    return __builtin_popcount(v);
+#endif
+}
+
+// class of a low / high half string (popcount, or popcount * 8 + irrep)
+__host__ __device__ __forceinline__ int half_cls(uint32_t s, int irr, const uint32_t *m) {
+    int c = ps_popc32(s);
+    if (irr)
+        c = (c << 3) | (ps_popc32(s & m[0]) & 1) | ((ps_popc32(s & m[1]) & 1) << 1) |
+            ((ps_popc32(s & m[2]) & 1) << 2);
+    return c;
+}
+__host__ __device__ __forceinline__ int cls_lo(const SectorView &v, uint32_t s) { return half_cls(s, v.irr, v.irr_lo); }
+__host__ __device__ __forceinline__ int cls_hi(const SectorView &v, uint32_t s) { return half_cls(s, v.irr, v.irr_hi); }
 
 // ---------------------------------------------------------------------------
 // apply plan: the canonical sum re-laid out for one sector split (rows = high

@@ -97,7 +97,7 @@ k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
         rrank[0] = i;
         if (MODE == RS_PAIR) {
             const uint32_t r2 = rpat[0] ^ (uint32_t)A.xh;
-            if (__popc(r2) == khi) {
+            if (cls_hi(v, r2) == khi) {
                 const int64_t j = __ldg(v.rank_hi + r2);
                 if (j < i) return;  // the partner row's block owns this pair of rows
                 rpat[1] = r2;
@@ -142,7 +142,7 @@ k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
             const uint64_t s = t ^ g.x;
             const uint32_t slo = (uint32_t)(s & lomask), shi = (uint32_t)(s >> v.n_lo);
             phase_sum<R>(A, g, s, fr, fi);
-            bool in = __popc(slo) == klo && __popc(shi) == khi;
+            bool in = cls_lo(v, slo) == klo && cls_hi(v, shi) == khi;
             int64_t pe = 0;
             if (in) {
                 if (MODE == RS_COL) {

@@ -10,6 +10,7 @@
 // binomial table below is that ranking's only constant; the apply kernels read
 // per-half lookup tables that k_rank_table fills with the same function.
 #include <algorithm>
+#include <vector>
 
 #include "ps_internal.cuh"
 
@@ -82,8 +83,13 @@ __global__ void k_sector_rank(SectorView v, const uint64_t *cfg, int64_t n, int6
     if ((b >> v.n) != 0) { idx[i] = -1; return; }
     uint32_t lo = (uint32_t)(b & ((1ull << v.n_lo) - 1ull));
     uint32_t hi = (uint32_t)(b >> v.n_lo);
-    int blk = v.blk_of_khi[__popc(hi)];
-    if (blk < 0 || __popc(lo) != v.klo[blk]) { idx[i] = -1; return; }
+    int blk = v.blk_of_khi[cls_hi(v, hi)];
+    if (blk < 0 || cls_lo(v, lo) != v.klo[blk]) { idx[i] = -1; return; }
+    if (v.irr) {
+        // ranks inside (popcount, irrep) classes come from the tables
+        idx[i] = v.off[blk] + (int64_t)v.rank_hi[hi] * v.dlo[blk] + (int64_t)v.rank_lo[lo];
+        return;
+    }
     idx[i] = v.off[blk] + (int64_t)colex_rank(hi) * v.dlo[blk] + (int64_t)colex_rank(lo);
 }
 
@@ -98,8 +104,14 @@ __global__ void k_sector_unrank(SectorView v, const int64_t *idx, int64_t n, uin
     int64_t rem = k - v.off[blk];
     uint64_t rhi = (uint64_t)(rem / v.dlo[blk]);
     uint64_t rlo = (uint64_t)(rem % v.dlo[blk]);
-    uint32_t hi = colex_unrank(v.n_hi, v.khi[blk], rhi);
-    uint32_t lo = colex_unrank(v.n_lo, v.klo[blk], rlo);
+    uint32_t hi, lo;
+    if (v.irr) {
+        hi = v.list_hi[v.list_hi_off[v.khi[blk]] + rhi];
+        lo = v.list_lo[v.list_lo_off[v.klo[blk]] + rlo];
+    } else {
+        hi = colex_unrank(v.n_hi, v.khi[blk], rhi);
+        lo = colex_unrank(v.n_lo, v.klo[blk], rlo);
+    }
     cfg[i] = (uint64_t)lo | ((uint64_t)hi << v.n_lo);
 }
 
@@ -124,6 +136,29 @@ void build_sector_tables(pauli_sector *s, cudaStream_t st) {
     s->tables = static_cast<uint32_t *>(dev_alloc(s->al, total * sizeof(uint32_t)));
     uint32_t *rank_lo = s->tables, *list_lo = rank_lo + nlo;
     uint32_t *rank_hi = list_lo + nlo, *list_hi = rank_hi + nhi;
+    if (v.irr) {
+        // (popcount, irrep) classes: ranks and lists by counting on the host
+        for (int half = 0; half < 2; ++half) {
+            const int bits = half ? v.n_hi : v.n_lo;
+            const uint32_t *m = half ? v.irr_hi : v.irr_lo;
+            int64_t *off = half ? v.list_hi_off : v.list_lo_off;
+            const int64_t cnt = 1ll << bits;
+            std::vector<uint32_t> rk(cnt), ls(cnt);
+            std::vector<int64_t> count(kMaxCls + 1, 0);
+            for (int64_t t = 0; t < cnt; ++t) rk[t] = (uint32_t)count[half_cls((uint32_t)t, 1, m)]++;
+            off[0] = 0;
+            for (int c = 0; c < kMaxCls; ++c) off[c + 1] = off[c] + count[c];
+            for (int64_t t = 0; t < cnt; ++t) ls[off[half_cls((uint32_t)t, 1, m)] + rk[t]] = (uint32_t)t;
+            PS_CUDA(cudaMemcpyAsync(half ? rank_hi : rank_lo, rk.data(), cnt * 4, cudaMemcpyHostToDevice, st));
+            PS_CUDA(cudaMemcpyAsync(half ? list_hi : list_lo, ls.data(), cnt * 4, cudaMemcpyHostToDevice, st));
+            PS_CUDA(cudaStreamSynchronize(st));
+        }
+        v.rank_lo = rank_lo;
+        v.list_lo = list_lo;
+        v.rank_hi = rank_hi;
+        v.list_hi = list_hi;
+        return;
+    }
     for (int half = 0; half < 2; ++half) {
         const int bits = half ? v.n_hi : v.n_lo;
         int64_t *off = half ? v.list_hi_off : v.list_lo_off;
@@ -161,13 +196,15 @@ void sector_unrank(const SectorView &v, const int64_t *idx, int64_t n, uint64_t 
     PS_LAUNCH_CHECK();
 }
 
-// host-side geometry of a sector (dimensions, offsets, block lookup)
-void init_sector_view(SectorView &v, int n, int kind, int n_lo, int nb, const int *klo,
-                      const int *khi) {
+// host-side geometry of a sector (dimensions, offsets, block lookup).  With
+// qubit_irrep (n labels 0..7; point-group blocks) klo / khi are the classes
+// popcount * 8 + irrep of each block's halves, else popcounts.
+void init_sector_view(SectorView &v, int n, int kind, int n_lo, int nb, const int *klo, const int *khi,
+                      const int *qubit_irrep) {
     v = SectorView();
     v.n = n;
     v.kind = kind;
-    for (int i = 0; i < kMaxHalf + 9; ++i) v.blk_of_khi[i] = -1;
+    for (int i = 0; i < kMaxCls; ++i) v.blk_of_khi[i] = -1;
     if (kind == PAULI_SECTOR_FULL) {
         v.n_lo = n_lo;
         v.n_hi = n - n_lo;
@@ -185,12 +222,27 @@ void init_sector_view(SectorView &v, int n, int kind, int n_lo, int nb, const in
     v.n_lo = n_lo;
     v.n_hi = n - n_lo;
     v.nblk = nb;
+    std::vector<int64_t> cnt_lo, cnt_hi;
+    if (qubit_irrep) {
+        v.irr = 1;
+        for (int j = 0; j < 3; ++j) {
+            v.irr_lo[j] = v.irr_hi[j] = 0u;
+            for (int q = 0; q < v.n_lo; ++q)
+                if ((qubit_irrep[q] >> j) & 1) v.irr_lo[j] |= 1u << q;
+            for (int q = 0; q < v.n_hi; ++q)
+                if ((qubit_irrep[v.n_lo + q] >> j) & 1) v.irr_hi[j] |= 1u << q;
+        }
+        cnt_lo.assign(kMaxCls, 0);
+        cnt_hi.assign(kMaxCls, 0);
+        for (int64_t t = 0; t < (1ll << v.n_lo); ++t) ++cnt_lo[half_cls((uint32_t)t, 1, v.irr_lo)];
+        for (int64_t t = 0; t < (1ll << v.n_hi); ++t) ++cnt_hi[half_cls((uint32_t)t, 1, v.irr_hi)];
+    }
     int64_t off = 0, row = 0;
     for (int r = 0; r < nb; ++r) {
         v.klo[r] = klo[r];
         v.khi[r] = khi[r];
-        v.dlo[r] = (int64_t)binom_host(v.n_lo, klo[r]);
-        v.dhi[r] = (int64_t)binom_host(v.n_hi, khi[r]);
+        v.dlo[r] = v.irr ? cnt_lo[klo[r]] : (int64_t)binom_host(v.n_lo, klo[r]);
+        v.dhi[r] = v.irr ? cnt_hi[khi[r]] : (int64_t)binom_host(v.n_hi, khi[r]);
         v.off[r] = off;
         v.row_off[r] = row;
         off += v.dlo[r] * v.dhi[r];

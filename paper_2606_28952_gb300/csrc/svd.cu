@@ -173,7 +173,7 @@ k_apply_svd(SectorView v, Geom geo, SvdDev d, int pc0, int pc1, int64_t fa_row0,
     if (v.n_lo <= 14) {
         uint16_t *lut = reinterpret_cast<uint16_t *>(tab);
         for (int s = tid; s < (1 << v.n_lo); s += kThreads)
-            lut[s] = (uint16_t)(__popc(s) == klo ? __ldg(v.rank_lo + s) : (uint32_t)dlo);
+            lut[s] = (uint16_t)(cls_lo(v, (uint32_t)s) == klo ? __ldg(v.rank_lo + s) : (uint32_t)dlo);
     } else {
         uint32_t *tabA = reinterpret_cast<uint32_t *>(tab);
         uint32_t *tabB = tabA + 256;
@@ -206,7 +206,7 @@ k_apply_svd(SectorView v, Geom geo, SvdDev d, int pc0, int pc1, int64_t fa_row0,
     for (int q = pc0; q < pc1; ++q) {
         const int g0 = __ldg(d.pc_g0 + q), g1 = __ldg(d.pc_g0 + q + 1);
         const uint32_t shi = rc.thi ^ d.groups[g0].x_hi;
-        if (__popc(shi) != khi) continue;  // the source row is outside the sector (block-uniform)
+        if (cls_hi(v, shi) != khi) continue;  // the source row is outside the sector (block-uniform)
         const int64_t base = v.off[0] + (int64_t)__ldg(v.rank_hi + shi) * dlo;
         for (int64_t r = tid; r < dlo; r += kThreads) {
             if (sizeof(C2) == 16) cp_async16(row + r, psi + base + r);
@@ -248,7 +248,7 @@ k_apply_svd(SectorView v, Geom geo, SvdDev d, int pc0, int pc1, int64_t fa_row0,
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
                 const uint32_t s = tlo[j] ^ (uint32_t)gr.x;
-                if (!act[j] || __popc(s) != klo) continue;  // source outside the block
+                if (!act[j] || cls_lo(v, s) != klo) continue;  // source outside the block
                 const C2 amp = row[ranked_index(rt, s)];
                 if (sizeof(R) == 4 && gr.w) {
                     // x = 0 group on the FP32 path: FP64 contraction, applied as hi + lo parts
@@ -338,7 +338,8 @@ void free_svd_plan(SvdPlan *sp) {
 // operator is complex, a rank exceeds kSvdMaxRank or the low half is wider
 // than 16 qubits).  Blocking.
 SvdPlan *build_svd_plan(pauli_sum *H, const SectorView &v, cudaStream_t st) {
-    if (!(v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1) || !H->real || H->m == 0 || v.n_lo > 16) return nullptr;
+    if (!(v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1) || !H->real || H->m == 0 || v.n_lo > (v.irr ? 14 : 16))
+        return nullptr;
     const int64_t M = H->m, G = H->G;
     std::vector<uint64_t> z(M), gx(G);
     std::vector<double2> c(M);

@@ -218,3 +218,70 @@ def test_sector_index_by_binary_search_above_28_qubits(n, n_lo, blocks):
     probes += [int(b) for b in rng.integers(0, 1 << n, 200, dtype=np.uint64)]
     probes = [p for p in probes if p not in inside]
     assert np.all(S.index(np.array(probes, dtype=np.uint64)) == -1)
+
+
+def _brute_irrep_sector(n, n_lo, blocks, qirr):
+    def irrep(v, first, bits):
+        g = 0
+        for j in range(bits):
+            if (v >> j) & 1:
+                g ^= qirr[first + j]
+        return g
+    n_hi = n - n_lo
+    cfg = []
+    for kl, il, kh, ih in blocks:
+        los = [v for v in range(1 << n_lo) if bin(v).count("1") == kl and irrep(v, 0, n_lo) == il]
+        his = [v for v in range(1 << n_hi) if bin(v).count("1") == kh and irrep(v, n_lo, n_hi) == ih]
+        cfg += [lo | (hi << n_lo) for hi in his for lo in los]
+    return cfg
+
+
+@pytest.mark.parametrize("norb,na,nb,gamma", [(6, 3, 3, 0), (7, 2, 4, 5), (15, 1, 2, 3)])
+def test_pointgroup_sector_enumeration(norb, na, nb, gamma):
+    """Point-group blocks (k_lo, irrep_lo, k_hi, irrep_hi): positions against a
+    brute-force enumeration written here (above 28 qubits via the binary search),
+    -1 outside, and the block dimensions summing to the (N_a, N_b) count split
+    by irrep."""
+    irr = w.orbital_irreps(norb)
+    qirr = np.concatenate([irr, irr])
+    blocks = w.pointgroup_blocks(norb, na, nb, gamma, irr)
+    S = oracle.Sector.irrep_blocks(2 * norb, norb, blocks, qirr)
+    cfg = _brute_irrep_sector(2 * norb, norb, blocks, qirr)
+    assert S.dim == len(cfg)
+    assert np.array_equal(S.configs(), np.array(cfg, dtype=np.uint64))
+    assert np.array_equal(S.index(np.array(cfg, dtype=np.uint64)), np.arange(len(cfg)))
+    # the sectors of all 8 total irreps partition the (N_a, N_b) block
+    tot = 0
+    for gg in range(8):
+        tot += oracle.Sector.irrep_blocks(2 * norb, norb, w.pointgroup_blocks(norb, na, nb, gg, irr), qirr).dim
+    assert tot == oracle.Sector.molecular(norb, na, nb).dim
+    inside = set(cfg)
+    rng = np.random.default_rng(norb)
+    probes = [int(v) for v in rng.integers(0, 1 << (2 * norb), 300, dtype=np.uint64) if int(v) not in inside]
+    assert np.all(S.index(np.array(probes, dtype=np.uint64)) == -1)
+
+
+@pytest.mark.parametrize("norb,na,nb", [(5, 2, 2), (6, 3, 2)])
+def test_pointgroup_hamiltonian_keeps_its_sectors(norb, na, nb):
+    """With integrals that respect the point group, H maps each irrep sector into
+    itself: the full-space apply of a state supported on one sector has no weight
+    outside it, and equals the oracle's sector apply there (dense check)."""
+    irr = w.orbital_irreps(norb, seed=4001)
+    qirr = np.concatenate([irr, irr])
+    h, g = w.pointgroup_integrals(norb, 3, irr)
+    H = oracle.jw_hamiltonian(norb, h, g, eps_drop=1e-12)
+    full = oracle.Sector.full(2 * norb)
+    for gamma in range(8):
+        blocks = w.pointgroup_blocks(norb, na, nb, gamma, irr)
+        if not blocks:
+            continue
+        S = oracle.Sector.irrep_blocks(2 * norb, norb, blocks, qirr)
+        cfg = S.configs()
+        psi = w.random_state(S.dim, 7 + gamma)
+        big = np.zeros(1 << (2 * norb), np.complex128)
+        big[cfg.astype(np.int64)] = psi
+        out_full = oracle.apply(full, H, big)
+        mask = np.ones(1 << (2 * norb), bool)
+        mask[cfg.astype(np.int64)] = False
+        assert np.abs(out_full[mask]).max() < 1e-12
+        assert np.allclose(out_full[cfg.astype(np.int64)], oracle.apply(S, H, psi), atol=1e-12, rtol=0)

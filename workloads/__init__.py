@@ -323,3 +323,42 @@ def uccsd_trotter_order(pool, norb: int):
         modes = sorted({m for m, _ in terms[0][1] if m >= norb})
         return (2, tuple(modes))
     return sorted(pool, key=key)  # stable: the pool's order inside each class
+
+
+# ----------------------------------------------------------------------------
+# abelian point-group symmetry (synthetic irrep labels)
+# ----------------------------------------------------------------------------
+def orbital_irreps(norb: int, seed: int = 4000, n_irreps: int = 8) -> np.ndarray:
+    """Seeded irrep label (0..n_irreps-1, an abelian group of order 8 such as
+    D2h, product = XOR) of every spatial orbital."""
+    return np.random.default_rng(seed).integers(0, n_irreps, norb).astype(np.int32)
+
+
+def pointgroup_integrals(norb: int, seed: int, irreps) -> tuple[np.ndarray, np.ndarray]:
+    """The molecular generator's integrals with the entries that the point group
+    forbids set to zero: h_pq unless irrep(p) = irrep(q), (pq|rs) unless
+    irrep(p) ^ irrep(q) ^ irrep(r) ^ irrep(s) = 0."""
+    h, g = molecular_integrals(norb, seed)
+    ir = np.asarray(irreps)
+    h = np.where(ir[:, None] == ir[None, :], h, 0.0)
+    sym = (ir[:, None, None, None] ^ ir[None, :, None, None] ^ ir[None, None, :, None] ^ ir[None, None, None, :]) == 0
+    g = np.where(sym, g, 0.0)
+    return h, g
+
+
+def pointgroup_blocks(norb: int, na: int, nb: int, total_irrep: int, irreps):
+    """The nonempty blocks (k_lo, irrep_lo, k_hi, irrep_hi) of the sector with na
+    alpha and nb beta electrons and total irrep `total_irrep`, alpha irrep
+    ascending (blocked spin order: alpha = low half)."""
+    from itertools import combinations
+    ir = [int(v) for v in irreps]
+    def present(k):
+        out = set()
+        for c in combinations(range(norb), k):
+            g = 0
+            for p in c:
+                g ^= ir[p]
+            out.add(g)
+        return out
+    pa, pb = present(na), present(nb)
+    return [(na, ga, nb, ga ^ total_irrep) for ga in range(8) if ga in pa and (ga ^ total_irrep) in pb]
