@@ -381,8 +381,9 @@ def run_ours(args, rank, world, local_rank):
         side_wl["xxz30_sz0_apply_c64"] = xxz_apply_measure(ps, dev, w.XXZ_SITES, True, reps=20)
         side_wl["batched64_c64"] = batched_measure(
             ps, dev, warmup=1, steps=3, seeded_states=False,
-            shape=ps.LaunchConfig(cols_per_thread=4, staged_rows=1, row_split=1, direct=0, ranked=1, ms=0.0))
+            shape=ps.LaunchConfig(cols_per_thread=0, staged_rows=1, row_split=1, direct=0, ranked=0, ms=0.0))
         side_wl["mol32_apply_c64"] = mol32_apply_measure(ps, dev, reps=2)
+        side_wl["uccsd_trotter_24q_c64"] = uccsd_measure(ps, dev, reps=5)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -692,6 +693,58 @@ def xxz_apply_measure(ps, dev, n: int, sz0: bool, n_lo: int = 0, warmup: int = 3
     del psi, out
     torch.cuda.empty_cache()
     return r
+
+
+def uccsd_measure(ps, dev, reps: int = 5):
+    """The 24-qubit molecule's UCCSD generators (1,818 single and double
+    excitations): one Trotter step psi <- prod_k exp(-i theta_k G_k) psi applied
+    tile by tile (pauli_rotseq) against 1,818 separate rotations
+    (pauli_rotate_seq), complex64, random angles in [-0.3, 0.3]; and the ADAPT
+    pool gradients of all 1,818 generators at a random state (one launch)."""
+    import torch
+    norb, na, nb = 12, 6, 6
+    pool = w.uccsd_trotter_order(w.uccsd_pool(norb, na, nb), norb)
+    gens = [ps.PauliSum.jw_fermion(2 * norb, t) for _, t in pool]
+    S = ps.Sector.molecular(norb, na, nb)
+    h, g = w.MOL24.integrals()
+    H = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    thetas = np.random.default_rng(24).uniform(-0.3, 0.3, len(gens))
+    Q = ps.RotSeq(gens, S)
+    psi = torch.from_numpy(w.random_state(S.dim, 24)).to(dev, torch.complex64)
+    x = psi.clone()
+    stream = torch.cuda.current_stream()
+    Q.apply(thetas, x)
+    ps.rotate_seq(gens, S, thetas, x)  # first use builds the pair tables
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        Q.apply(thetas, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_fused = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for _ in range(reps):
+        ps.rotate_seq(gens, S, thetas, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / reps
+    P = ps.Pool(gens, S)
+    hx = torch.empty_like(psi)
+    ps.expect(H, S, psi, hpsi_out=hx)
+    out = torch.empty(len(gens), dtype=torch.float64, device=dev)
+    P.gradients(psi, hx, out)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        P.gradients(psi, hx, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pool = e0.elapsed_time(e1) / reps
+    info = Q.info(torch.complex64)
+    return {"generators": len(gens), "fused_launches": info["launches"], "fused_ms": t_fused,
+            "separate_rotations_ms": t_seq, "speedup": t_seq / t_fused, "pool_gradients_ms": t_pool,
+            "pool_gradients_per_s": len(gens) / t_pool * 1e3}
 
 
 def mol32_apply_measure(ps, dev, reps: int = 2):

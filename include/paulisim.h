@@ -504,12 +504,14 @@ int pauli_tune_load(pauli_sum *H, const pauli_sector *s, const char *path, int *
 /* ------------------------------------------------------------------------- */
 
 /* A batch of n (operator, sector) pairs -- e.g. the points of a scan or the
- * parameter-shifted states of a gradient -- applied together: one grid of
- * resident CTAs pulls (state, row, column tile) work units from an atomic
- * queue, largest states first, so states of very different sizes share the
- * GPU in one launch.  Every sector must be a single product block; the
- * handles must outlive the batch; pauli_batch_create calls pauli_prepare on
- * each pair. */
+ * parameter-shifted states of a gradient -- applied together in persistent
+ * launches: a grid of resident CTAs pulls (state, row, column tile) work
+ * units from an atomic queue, largest states first.  By default every state
+ * keeps the staged-gather shape a launch of its own would take, and the
+ * states of one shape share one persistent launch (one launch per distinct
+ * shape); a uniform shape can be installed or tuned instead.  Every sector
+ * must be a single product block; the handles must outlive the batch;
+ * pauli_batch_create calls pauli_prepare on each pair. */
 typedef struct pauli_batch pauli_batch;
 int pauli_batch_create(int n, pauli_sum *const *H, const pauli_sector *const *S, int dtype,
                        pauli_batch **out);
@@ -522,16 +524,18 @@ int pauli_batch_create(int n, pauli_sum *const *H, const pauli_sector *const *S,
 int pauli_batch_apply(pauli_batch *b, const void *const *psi_in, void *const *psi_out, double *results,
                       pauli_stream_t st);
 
-/* Times the batched launch for every columns-per-thread / staged-rows shape on
- * the given vectors and keeps the fastest.  Blocking. */
+/* Times the per-state shapes and every uniform columns-per-thread /
+ * staged-rows / staging layout on the given vectors and keeps the fastest
+ * (best->cols_per_thread = 0 for the per-state shapes).  Blocking. */
 int pauli_batch_tune(pauli_batch *b, const void *const *psi_in, void *const *psi_out, int reps,
                      pauli_launch_config *best, pauli_stream_t st);
 
-/* Installs a launch shape for the batch (cols_per_thread 1, 2 or 4,
- * staged_rows 1 or 2, ranked 0 or 1; row_split must be 1 and direct 0):
+/* Installs a uniform launch shape for the batch (cols_per_thread 1, 2 or 4,
+ * staged_rows 1 or 2, ranked 0 or 1; row_split must be 1 and direct 0), or,
+ * with cols_per_thread = 0, goes back to the per-state shapes:
  * PAULI_EUNSUPPORTED if the staging layout does not fit in shared memory for
  * the widest state.  pauli_batch_get_launch_config reads the shape in use
- * (ms = 0). */
+ * (cols_per_thread = 0 for per-state shapes; ms = launches per apply). */
 int pauli_batch_set_launch_config(pauli_batch *b, const pauli_launch_config *cfg);
 int pauli_batch_get_launch_config(const pauli_batch *b, pauli_launch_config *cfg);
 

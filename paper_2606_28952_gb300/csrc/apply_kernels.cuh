@@ -665,8 +665,11 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
     }
 }
 
+// FP32 path: register budget of four resident CTAs (64 registers a thread),
+// the allocation measured fastest on the 24-qubit molecule (the compiler's own
+// choice for this body spills); the FP64 path keeps the compiler's choice.
 template <typename R, int KIND, bool REALH, int TPT, int NBUF>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
 k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
         typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
     extern __shared__ __align__(16) char smem[];

@@ -1,5 +1,12 @@
 // batch.cu -- many independent states, each with its own operator and sector,
-// in one persistent launch: H_b psi_b and <psi_b|H_b|psi_b> for every b.
+// in persistent launches: H_b psi_b and <psi_b|H_b|psi_b> for every b.
+//
+// By default every state keeps the staged-gather shape a launch of its own
+// would take (columns per thread, staged rows in flight, rows staged by bit
+// pattern or by rank); states are grouped by shape, largest first inside a
+// group, and each group is one persistent launch whose CTAs pull (state, row,
+// column tile) units from an atomic counter.  A uniform shape for all states
+// can be installed or found by the tuner instead.
 #include <algorithm>
 #include <cfloat>
 #include <numeric>
@@ -20,9 +27,19 @@ struct pauli_batch {
     std::vector<int64_t> rw_bits;     // n_lo per state
     int max_nlo = 0;
     int64_t max_dlo = 0;
-    int64_t total = 0;                // work units of one launch
-    int tpt = 0, nbuf = 1;            // launch shape (0: not chosen yet)
+    int64_t total = 0;                // work units of all launches
+    bool grouped = true;              // per-state shapes (one launch per shape group)
+    int tpt = 0, nbuf = 1;            // the uniform shape (grouped == false)
     bool ranked = false;              // rows staged by rank (wide splits)
+    struct Group {
+        int tpt, nbuf;
+        bool ranked;
+        int q0, q1;                   // queue positions of the group's states
+        int64_t total;                // work units of the group's launch
+        int max_nlo;
+        int64_t max_dlo;
+    };
+    std::vector<Group> groups;
     BatchDesc *d_desc = nullptr;      // [n] in queue order
     BatchPtrs *d_ptrs = nullptr;      // [n]
     double *d_partials = nullptr;     // [total][4]
@@ -36,94 +53,147 @@ namespace ps_batch {
 constexpr uint32_t kBatchMagic = 0x50424131u;
 
 template <typename R, int KIND, bool REALH, int TPT, int NBUF>
-void launch_batch_t(pauli_batch *b, size_t smem, double *results, bool want_out, cudaStream_t st) {
+void launch_group_t(pauli_batch *b, const pauli_batch::Group &g, size_t smem, bool want_out, cudaStream_t st) {
     auto kern = k_apply_batch<R, KIND, REALH, TPT, NBUF>;
     smem_optin(reinterpret_cast<const void *>(kern), smem);
     int per_sm = 0;
     PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     const int sms = num_sms();
     PS_CHECK(per_sm >= 1, PAULI_EUNSUPPORTED, "batched apply: the launch shape does not fit on an SM");
-    const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, std::max<int64_t>(1, b->total));
+    if (g.total <= 0) return;
+    const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, g.total);
     PS_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st));
-    kern<<<(unsigned)grid, kThreads, smem, st>>>(b->d_desc, b->d_ptrs, b->n, b->total, b->d_counter, b->d_partials,
-                                                 want_out ? 1 : 0);
-    PS_LAUNCH_CHECK();
-    k_batch_reduce<<<b->n, 256, 0, st>>>(b->d_desc, b->d_partials, results);
+    kern<<<(unsigned)grid, kThreads, smem, st>>>(b->d_desc + g.q0, b->d_ptrs + g.q0, g.q1 - g.q0, g.total,
+                                                 b->d_counter, b->d_partials, want_out ? 1 : 0);
     PS_LAUNCH_CHECK();
 }
 
-// Dynamic shared memory of the batched launch: the widest state decides.
-size_t batch_smem(const pauli_batch *b, int nbuf, bool ranked) {
+// Dynamic shared memory of a group's launch: its widest state decides.
+size_t group_smem(const pauli_batch *b, int nbuf, bool ranked, int max_nlo, int64_t max_dlo) {
     auto bb = [&](int cap) {
         return b->dtype == PAULI_C64 ? Smem<float>::buf_bytes(cap) : Smem<double>::buf_bytes(cap);
     };
-    if (!ranked) return (size_t)nbuf * bb(1 << b->max_nlo);
-    return (size_t)nbuf * bb(ranked_rowcap(b->max_dlo)) + rank_table_bytes(b->max_nlo);
+    if (!ranked) return (size_t)nbuf * bb(1 << max_nlo);
+    return (size_t)nbuf * bb(ranked_rowcap(max_dlo)) + rank_table_bytes(max_nlo);
+}
+size_t batch_smem(const pauli_batch *b, int nbuf, bool ranked) {
+    return group_smem(b, nbuf, ranked, b->max_nlo, b->max_dlo);
 }
 
 template <typename R, int KIND, bool REALH>
-void launch_batch_k(pauli_batch *b, int tpt, int nbuf, double *results, bool want_out, cudaStream_t st) {
-    const size_t smem = batch_smem(b, nbuf, KIND == KBLKR);
+void launch_group_k(pauli_batch *b, const pauli_batch::Group &g, bool want_out, cudaStream_t st) {
+    const size_t smem = group_smem(b, g.nbuf, KIND == KBLKR, g.max_nlo, g.max_dlo);
     PS_CHECK(smem <= 226 * 1024, PAULI_EUNSUPPORTED, "batched apply: the widest sector split is too wide");
-#define PS_B(T, N) launch_batch_t<R, KIND, REALH, T, N>(b, smem, results, want_out, st)
-    if (nbuf == 2) {
-        if (tpt == 4) PS_B(4, 2); else if (tpt == 2) PS_B(2, 2); else PS_B(1, 2);
+#define PS_B(T, N) launch_group_t<R, KIND, REALH, T, N>(b, g, smem, want_out, st)
+    if (g.nbuf == 2) {
+        if (g.tpt == 4) PS_B(4, 2); else if (g.tpt == 2) PS_B(2, 2); else PS_B(1, 2);
     } else {
-        if (tpt == 4) PS_B(4, 1); else if (tpt == 2) PS_B(2, 1); else PS_B(1, 1);
+        if (g.tpt == 4) PS_B(4, 1); else if (g.tpt == 2) PS_B(2, 1); else PS_B(1, 1);
     }
 #undef PS_B
 }
 
 template <typename R>
-void launch_batch_r(pauli_batch *b, int tpt, int nbuf, bool ranked, double *results, bool want_out, cudaStream_t st) {
-    if (ranked) {
-        if (b->realh) launch_batch_k<R, KBLKR, true>(b, tpt, nbuf, results, want_out, st);
-        else launch_batch_k<R, KBLKR, false>(b, tpt, nbuf, results, want_out, st);
+void launch_group_r(pauli_batch *b, const pauli_batch::Group &g, bool want_out, cudaStream_t st) {
+    if (g.ranked) {
+        if (b->realh) launch_group_k<R, KBLKR, true>(b, g, want_out, st);
+        else launch_group_k<R, KBLKR, false>(b, g, want_out, st);
     } else {
-        if (b->realh) launch_batch_k<R, KBLK1, true>(b, tpt, nbuf, results, want_out, st);
-        else launch_batch_k<R, KBLK1, false>(b, tpt, nbuf, results, want_out, st);
+        if (b->realh) launch_group_k<R, KBLK1, true>(b, g, want_out, st);
+        else launch_group_k<R, KBLK1, false>(b, g, want_out, st);
     }
 }
 
-void launch_batch(pauli_batch *b, int tpt, int nbuf, bool ranked, double *results, bool want_out, cudaStream_t st) {
-    if (b->dtype == PAULI_C64) launch_batch_r<float>(b, tpt, nbuf, ranked, results, want_out, st);
-    else launch_batch_r<double>(b, tpt, nbuf, ranked, results, want_out, st);
+// every group's launch, then the fixed-order reduction of every state's partials
+void launch_batch(pauli_batch *b, double *results, bool want_out, cudaStream_t st) {
+    for (const auto &g : b->groups) {
+        if (b->dtype == PAULI_C64) launch_group_r<float>(b, g, want_out, st);
+        else launch_group_r<double>(b, g, want_out, st);
+    }
+    k_batch_reduce<<<b->n, 256, 0, st>>>(b->d_desc, b->d_partials, results);
+    PS_LAUNCH_CHECK();
 }
 
-// (Re)build the descriptors for a columns-per-thread value.
-void build_descs(pauli_batch *b, int tpt) {
-    std::vector<BatchDesc> h(b->n);
-    std::vector<int64_t> nwork(b->n);
+// The staged-gather shape a launch of its own would give state i (its tuned or
+// heuristic shape; a list / direct / SVD choice is replaced by the staged one).
+void state_shape(pauli_batch *b, int i, int &tpt, int &nbuf, bool &ranked) {
+    const SectorView &v = b->S[i]->v;
+    Plan *p = find_plan(b->H[i], v);
+    PS_CHECK(p != nullptr, PAULI_EINVAL, "batched apply: a plan is missing (internal)");
+    ApplyCfg c = apply_config(*p, v, b->dtype, false);
+    if (c.list || c.direct || c.svd || c.local) {
+        LaunchChoice f;
+        f.direct = 0;
+        c = apply_config(*p, v, b->dtype, false, &f);
+    }
+    tpt = c.tpt >= 4 ? 4 : c.tpt;  // the batched kernel has 1, 2 or 4 columns per thread
+    nbuf = c.nbuf;
+    ranked = c.ranked;
+}
+
+// (Re)build the queue: shape groups (per state, or one uniform shape), states
+// largest first inside a group, descriptors and partial slots.
+void build_descs(pauli_batch *b) {
+    struct St {
+        int i, tpt, nbuf;
+        bool ranked;
+        int64_t nwork;
+    };
+    std::vector<St> st(b->n);
     for (int i = 0; i < b->n; ++i) {
+        St &e = st[i];
+        e.i = i;
+        if (b->grouped) {
+            state_shape(b, i, e.tpt, e.nbuf, e.ranked);
+        } else {
+            e.tpt = b->tpt;
+            e.nbuf = b->nbuf;
+            e.ranked = b->ranked;
+        }
         const SectorView &v = b->S[i]->v;
-        nwork[i] = make_geom(v, tpt * kThreads).cta_off[v.nblk];
+        e.nwork = make_geom(v, e.tpt * kThreads).cta_off[v.nblk];
     }
+    std::stable_sort(st.begin(), st.end(), [](const St &a, const St &c) {
+        if (a.ranked != c.ranked) return a.ranked < c.ranked;
+        if (a.tpt != c.tpt) return a.tpt > c.tpt;
+        if (a.nbuf != c.nbuf) return a.nbuf < c.nbuf;
+        return a.nwork > c.nwork;
+    });
+    std::vector<BatchDesc> h(b->n);
     b->order.resize(b->n);
-    std::iota(b->order.begin(), b->order.end(), 0);
-    std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return nwork[a] > nwork[c]; });
-    int64_t w0 = 0;
+    b->groups.clear();
+    int64_t part = 0;
     for (int q = 0; q < b->n; ++q) {
-        const int i = b->order[q];
+        const St &e = st[q];
+        if (b->groups.empty() || b->groups.back().tpt != e.tpt || b->groups.back().nbuf != e.nbuf ||
+            b->groups.back().ranked != e.ranked)
+            b->groups.push_back({e.tpt, e.nbuf, e.ranked, q, q, 0, 0, 0});
+        pauli_batch::Group &g = b->groups.back();
+        const int i = e.i;
         const SectorView &v = b->S[i]->v;
         Plan *p = find_plan(b->H[i], v);
         PS_CHECK(p != nullptr, PAULI_EINVAL, "batched apply: a plan is missing (internal)");
         BatchDesc d;
         d.v = v;
-        d.geo = make_geom(v, tpt * kThreads, 1, nullptr, (int32_t)p->P);
+        d.geo = make_geom(v, e.tpt * kThreads, 1, nullptr, (int32_t)p->P);
         d.p = plan_dev(*p);
-        d.work0 = w0;
-        d.nwork = nwork[i];
-        d.part0 = w0;
+        d.work0 = g.total;   // relative to the group's launch
+        d.nwork = e.nwork;
+        d.part0 = part;      // global partial slots
         h[q] = d;
-        w0 += nwork[i];
+        b->order[q] = i;
+        g.q1 = q + 1;
+        g.total += e.nwork;
+        g.max_nlo = std::max(g.max_nlo, v.n_lo);
+        g.max_dlo = std::max<int64_t>(g.max_dlo, v.dlo[0]);
+        part += e.nwork;
     }
-    b->total = w0;
+    b->total = part;
     dev_free(b->al, b->d_partials);
     b->d_partials = nullptr;
-    b->d_partials = static_cast<double *>(dev_alloc(b->al, (size_t)std::max<int64_t>(1, w0) * 4 * sizeof(double)));
+    b->d_partials = static_cast<double *>(dev_alloc(b->al, (size_t)std::max<int64_t>(1, part) * 4 * sizeof(double)));
     PS_CUDA(cudaMemcpy(b->d_desc, h.data(), sizeof(BatchDesc) * b->n, cudaMemcpyHostToDevice));
     PS_CUDA(cudaMemcpy(b->d_order, b->order.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));
-    b->tpt = tpt;
 }
 
 void upload_ptrs(pauli_batch *b, const void *const *psi_in, void *const *psi_out, cudaStream_t st) {
@@ -182,12 +252,12 @@ int pauli_batch_create(int n, pauli_sum *const *H, const pauli_sector *const *S,
             b->d_counter = static_cast<unsigned long long *>(dev_alloc(b->al, sizeof(unsigned long long)));
             b->d_order = static_cast<int *>(dev_alloc(b->al, sizeof(int) * n));
             b->h_ptrs.resize(n);
-            int64_t mx = 0;
-            for (int i = 0; i < n; ++i) mx = std::max<int64_t>(mx, S[i]->v.dlo[0]);
-            const int tpt = mx >= 3 * kThreads ? 4 : (mx >= 3 * kThreads / 2 ? 2 : 1);
-            build_descs(b, (tpt == 1 || tpt == 2 || tpt == 4) ? tpt : 1);
+            // per-state shapes by default (one persistent launch per shape group)
+            b->grouped = true;
+            b->tpt = 4;
             b->nbuf = 1;
             b->ranked = batch_smem(b, 1, false) > 226 * 1024;
+            build_descs(b);
         } catch (...) {
             dev_free(b->al, b->d_desc);
             dev_free(b->al, b->d_ptrs);
@@ -227,7 +297,7 @@ int pauli_batch_apply(pauli_batch *b, const void *const *psi_in, void *const *ps
         }
         cudaStream_t cs = (cudaStream_t)st;
         upload_ptrs(b, psi_in, psi_out, cs);
-        launch_batch(b, b->tpt, b->nbuf, b->ranked, b->d_results, psi_out != nullptr, cs);
+        launch_batch(b, b->d_results, psi_out != nullptr, cs);
         if (results) {  // results in the caller's state order
             k_unpermute<<<(b->n + 127) / 128, 128, 0, cs>>>(b->d_results, b->d_order, b->n, results);
             PS_LAUNCH_CHECK();
@@ -254,30 +324,42 @@ int pauli_batch_tune(pauli_batch *b, const void *const *psi_in, void *const *psi
         PS_CUDA(cudaEventCreate(&e0));
         PS_CUDA(cudaEventCreate(&e1));
         double best_ms = DBL_MAX;
+        bool bg = b->grouped;
         int bt = b->tpt, bn = b->nbuf;
         bool br = b->ranked;
+        // candidates: the per-state shapes, and every uniform shape that fits
+        struct Cand {
+            bool grouped;
+            int tpt, nbuf;
+            bool ranked;
+        };
+        std::vector<Cand> cands{{true, 4, 1, false}};
+        for (int tpt : {1, 2, 4})
+            for (int ranked : {0, 1})
+                for (int nbuf : {1, 2})
+                    if (batch_smem(b, nbuf, ranked != 0) <= 226 * 1024) cands.push_back({false, tpt, nbuf, ranked != 0});
         try {
-            for (int tpt : {1, 2, 4}) {
-                build_descs(b, tpt);
+            for (const Cand &c : cands) {
+                b->grouped = c.grouped;
+                b->tpt = c.tpt;
+                b->nbuf = c.nbuf;
+                b->ranked = c.ranked;
+                build_descs(b);
                 upload_ptrs(b, psi_in, psi_out, cs);
-                for (int ranked : {0, 1})
-                    for (int nbuf : {1, 2}) {
-                        if (batch_smem(b, nbuf, ranked != 0) > 226 * 1024) continue;
-                        launch_batch(b, tpt, nbuf, ranked != 0, b->d_results, psi_out != nullptr, cs);
-                        PS_CUDA(cudaEventRecord(e0, cs));
-                        for (int r = 0; r < reps; ++r)
-                            launch_batch(b, tpt, nbuf, ranked != 0, b->d_results, psi_out != nullptr, cs);
-                        PS_CUDA(cudaEventRecord(e1, cs));
-                        PS_CUDA(cudaEventSynchronize(e1));
-                        float ms = 0.f;
-                        PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                        if (ms / reps < best_ms) {
-                            best_ms = ms / reps;
-                            bt = tpt;
-                            bn = nbuf;
-                            br = ranked != 0;
-                        }
-                    }
+                launch_batch(b, b->d_results, psi_out != nullptr, cs);
+                PS_CUDA(cudaEventRecord(e0, cs));
+                for (int r = 0; r < reps; ++r) launch_batch(b, b->d_results, psi_out != nullptr, cs);
+                PS_CUDA(cudaEventRecord(e1, cs));
+                PS_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms / reps < best_ms) {
+                    best_ms = ms / reps;
+                    bg = c.grouped;
+                    bt = c.tpt;
+                    bn = c.nbuf;
+                    br = c.ranked;
+                }
             }
         } catch (...) {
             (void)cudaEventDestroy(e0);
@@ -286,15 +368,17 @@ int pauli_batch_tune(pauli_batch *b, const void *const *psi_in, void *const *psi
         }
         (void)cudaEventDestroy(e0);
         (void)cudaEventDestroy(e1);
-        build_descs(b, bt);
+        b->grouped = bg;
+        b->tpt = bt;
         b->nbuf = bn;
         b->ranked = br;
+        build_descs(b);
         if (best) {
-            best->cols_per_thread = bt;
-            best->staged_rows = bn;
+            best->cols_per_thread = bg ? 0 : bt;
+            best->staged_rows = bg ? 0 : bn;
             best->row_split = 1;
             best->direct = 0;
-            best->ranked = br ? 1 : 0;
+            best->ranked = bg ? 0 : (br ? 1 : 0);
             best->ms = best_ms;
         }
         return PAULI_OK;
@@ -312,17 +396,24 @@ int pauli_batch_set_launch_config(pauli_batch *b, const pauli_launch_config *cfg
         clear_error();
         PS_CHECK(b && b->magic == kBatchMagic, PAULI_EINVAL, "not a valid pauli_batch handle");
         PS_CHECK(cfg != nullptr, PAULI_EINVAL, "cfg is NULL");
+        if (cfg->cols_per_thread == 0) {  // back to per-state shapes
+            b->grouped = true;
+            build_descs(b);
+            return PAULI_OK;
+        }
         PS_CHECK(cfg->cols_per_thread == 1 || cfg->cols_per_thread == 2 || cfg->cols_per_thread == 4, PAULI_EINVAL,
-                 "batch: cols_per_thread must be 1, 2 or 4");
+                 "batch: cols_per_thread must be 0 (per-state shapes), 1, 2 or 4");
         PS_CHECK(cfg->staged_rows == 1 || cfg->staged_rows == 2, PAULI_EINVAL, "staged_rows must be 1 or 2");
         PS_CHECK(cfg->ranked == 0 || cfg->ranked == 1, PAULI_EINVAL, "ranked must be 0 or 1");
         PS_CHECK(cfg->row_split == 1 && cfg->direct == 0, PAULI_EUNSUPPORTED,
                  "batch: only the staged gather without row splits runs in the batched launch");
         PS_CHECK(batch_smem(b, cfg->staged_rows, cfg->ranked != 0) <= 226 * 1024, PAULI_EUNSUPPORTED,
                  "batch: this staging layout does not fit in shared memory for the widest state");
-        build_descs(b, cfg->cols_per_thread);
+        b->grouped = false;
+        b->tpt = cfg->cols_per_thread;
         b->nbuf = cfg->staged_rows;
         b->ranked = cfg->ranked != 0;
+        build_descs(b);
         return PAULI_OK;
     } catch (const Error &e) {
         set_error(e.msg);
@@ -339,12 +430,12 @@ int pauli_batch_get_launch_config(const pauli_batch *b, pauli_launch_config *cfg
         return PAULI_EINVAL;
     }
     clear_error();
-    cfg->cols_per_thread = b->tpt;
-    cfg->staged_rows = b->nbuf;
+    cfg->cols_per_thread = b->grouped ? 0 : b->tpt;
+    cfg->staged_rows = b->grouped ? 0 : b->nbuf;
     cfg->row_split = 1;
     cfg->direct = 0;
-    cfg->ranked = b->ranked ? 1 : 0;
-    cfg->ms = 0.0;
+    cfg->ranked = b->grouped ? 0 : (b->ranked ? 1 : 0);
+    cfg->ms = (double)b->groups.size();  // launches per apply
     return PAULI_OK;
 }
 

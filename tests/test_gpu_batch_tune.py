@@ -69,7 +69,7 @@ def test_batch_tune_keeps_results(ps, small_batch):
     B = ps.Batch(Hs, Ss, dtype=torch.complex64)
     before = B.apply(xs).cpu().numpy()
     cfg = B.tune(xs, reps=2)
-    assert cfg["cols_per_thread"] in (1, 2, 4) and cfg["staged_rows"] in (1, 2) and cfg["ms"] > 0
+    assert cfg["cols_per_thread"] in (0, 1, 2, 4) and cfg["staged_rows"] in (0, 1, 2) and cfg["ms"] > 0
     after = B.apply(xs).cpu().numpy()
     assert np.allclose(after, before, rtol=1e-5, atol=1e-6)
 

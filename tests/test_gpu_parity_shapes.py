@@ -236,7 +236,8 @@ def test_batched_64_full_size_sampled_rows(ps):
         So = oracle.Sector.molecular(m.norb, m.n_alpha, m.n_beta)
         refs.append(oracle_rows(So, Ros[b], psis[b].astype(np.complex128), samples[b]))
         del So
-    shapes = [None, ps.LaunchConfig(cols_per_thread=4, staged_rows=1, row_split=1, direct=0, ranked=1, ms=0.0),
+    shapes = [None, ps.LaunchConfig(cols_per_thread=0, staged_rows=1, row_split=1, direct=0, ranked=0, ms=0.0),
+              ps.LaunchConfig(cols_per_thread=4, staged_rows=1, row_split=1, direct=0, ranked=1, ms=0.0),
               ps.LaunchConfig(cols_per_thread=4, staged_rows=1, row_split=1, direct=0, ranked=0, ms=0.0)]
     ran = []
     for shp in shapes:
@@ -251,6 +252,7 @@ def test_batched_64_full_size_sampled_rows(ps):
             assert _rel(sub, refs[b]) <= TOL["c64"], (b, ran[-1])
             assert np.isfinite(res[b]).all()
     assert tuned["ms"] > 0 and {r["ranked"] for r in ran} == {0, 1}
+    assert ran[1]["cols_per_thread"] == 0 and ran[1]["ms"] >= 2  # per-state shapes: one launch per shape group
 
 
 # ----------------------------------------------------------------------------
