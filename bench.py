@@ -381,7 +381,9 @@ def run_ours(args, rank, world, local_rank):
         side_wl["xxz30_sz0_apply_c64"] = xxz_apply_measure(ps, dev, w.XXZ_SITES, True, reps=20)
         side_wl["batched64_c64"] = batched_measure(
             ps, dev, warmup=1, steps=3, seeded_states=False,
-            shape=ps.LaunchConfig(cols_per_thread=0, staged_rows=1, row_split=1, direct=0, ranked=0, ms=0.0))
+            shape=ps.LaunchConfig(cols_per_thread=4, staged_rows=1, row_split=1, direct=0, ranked=1, ms=0.0),
+            alt_shapes={"per_state_shape_groups": ps.LaunchConfig(cols_per_thread=0, staged_rows=1, row_split=1,
+                                                                  direct=0, ranked=0, ms=0.0)})
         side_wl["mol32_apply_c64"] = mol32_apply_measure(ps, dev, reps=2)
         side_wl["uccsd_trotter_24q_c64"] = uccsd_measure(ps, dev, reps=5)
 
@@ -533,7 +535,8 @@ def run_xxz(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
-def batched_measure(ps, dev, warmup: int, steps: int, tune_reps: int = 2, shape=None, seeded_states=True):
+def batched_measure(ps, dev, warmup: int, steps: int, tune_reps: int = 2, shape=None, seeded_states=True,
+                    alt_shapes=None):
     """64 independent synthetic molecules (n_orb ~ U{8..14}, half filling): one
     persistent complex64 launch of H_b psi_b + <H>_b (FP64 reductions) against 64
     sequential complex128 and 64 sequential complex64 pauli_expect calls, all on
@@ -586,6 +589,18 @@ def batched_measure(ps, dev, warmup: int, steps: int, tune_reps: int = 2, shape=
     torch.cuda.synchronize()
     clk = clocks.stop()
     t_batch = e0.elapsed_time(e1) / 1e3 / steps
+    # other installed shapes, same states (informational)
+    alt = {}
+    for name, c in (alt_shapes or {}).items():
+        B.set_launch_config(c)
+        B.apply(x64, outs, res)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            B.apply(x64, outs, res)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        alt[name] = {"ms": e0.elapsed_time(e1) / steps, "launches": int(B.launch_config()["ms"])}
     # 64 sequential FP64 launches (one pauli_expect with H psi per state)
     r128 = torch.empty((64, 4), dtype=torch.float64, device=dev)
     h128 = [torch.empty_like(p) for p in psis]
@@ -622,6 +637,7 @@ def batched_measure(ps, dev, warmup: int, steps: int, tune_reps: int = 2, shape=
         "sequential_c128_ms": t_seq * 1e3, "speedup_vs_sequential_c128": t_seq / t_batch,
         "sequential_c64_ms": t_seq64 * 1e3, "speedup_vs_sequential_c64": t_seq64 / t_batch,
         "max_energy_diff_c64_vs_c128_Ha": dE, "clocks": clk, "peak": f"{peak_kind} {hbm_peak} GB/s",
+        "other_shapes": alt or None,
     }
 
 

@@ -24,6 +24,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import subprocess
+import threading
 from dataclasses import dataclass
 
 import numpy as np
@@ -51,9 +52,16 @@ _u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
 
+_lib_lock = threading.Lock()
+
+
 def lib():
     global _lib
-    if _lib is None:
+    if _lib is not None:
+        return _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
         L = C.CDLL(build())
         L.orc_letter_mul.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int)]
         L.orc_letter_mul.restype = C.c_int

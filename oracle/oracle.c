@@ -326,24 +326,24 @@ void orc_sum_product(int n, int64_t ma, const uint64_t *xa, const uint64_t *za, 
 /* ------------------------------------------------------------------------- */
 /* canonical reduction (Sec. 2.3)                                             */
 /* ------------------------------------------------------------------------- */
-static const uint64_t *g_kx, *g_kz;
-
-static int key_less(int64_t a, int64_t b)
+/* (x, z) key order of entries a and b (keys passed in: the sort holds no
+ * global state, so calls from several threads do not interfere) */
+static int key_less(const uint64_t *kx, const uint64_t *kz, int64_t a, int64_t b)
 {
-    if (g_kx[a] != g_kx[b]) return g_kx[a] < g_kx[b];
-    return g_kz[a] < g_kz[b];
+    if (kx[a] != kx[b]) return kx[a] < kx[b];
+    return kz[a] < kz[b];
 }
 
 /* plain top-down stable merge sort of an index array by the (x, z) key */
-static void msort(int64_t *idx, int64_t *tmp, int64_t n)
+static void msort(const uint64_t *kx, const uint64_t *kz, int64_t *idx, int64_t *tmp, int64_t n)
 {
     if (n < 2) return;
     int64_t h = n / 2;
-    msort(idx, tmp, h);
-    msort(idx + h, tmp, n - h);
+    msort(kx, kz, idx, tmp, h);
+    msort(kx, kz, idx + h, tmp, n - h);
     int64_t i = 0, j = h, k = 0;
     while (i < h && j < n) {
-        if (key_less(idx[j], idx[i])) tmp[k++] = idx[j++];
+        if (key_less(kx, kz, idx[j], idx[i])) tmp[k++] = idx[j++];
         else tmp[k++] = idx[i++];
     }
     while (i < h) tmp[k++] = idx[i++];
@@ -363,9 +363,7 @@ int64_t orc_canonical(int64_t m, const uint64_t *x, const uint64_t *z, const dou
     int64_t *idx = (int64_t *)malloc((size_t)m * sizeof(int64_t));
     int64_t *tmp = (int64_t *)malloc((size_t)m * sizeof(int64_t));
     for (int64_t i = 0; i < m; ++i) idx[i] = i;
-    g_kx = x;
-    g_kz = z;
-    msort(idx, tmp, m);
+    msort(x, z, idx, tmp, m);
     double eps2 = eps * eps;
     int64_t out = 0;
     int64_t i = 0;

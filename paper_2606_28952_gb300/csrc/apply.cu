@@ -51,7 +51,7 @@ k_rotate(SectorView v, Geom geo, int64_t m, uint64_t x, const uint64_t *__restri
     const uint32_t xlo = (uint32_t)(x & ((1ull << v.n_lo) - 1ull));
     const uint32_t xhi = (uint32_t)(x >> v.n_lo);
     uint32_t tlo = 0;
-    if (act) tlo = FULL ? (uint32_t)col : __ldg(v.list_lo + v.list_lo_off[v.klo[rc.blk]] + col);
+    if (act) tlo = FULL ? (uint32_t)col : __ldg(v.list_lo + v.lst_lo_off[rc.blk] + col);
     const uint32_t shi = rc.thi ^ xhi, slo = tlo ^ xlo;
     const uint64_t s = (uint64_t)slo | ((uint64_t)shi << v.n_lo);
     // f_t = sum_k C_k (-1)^popcount(z_k & s)
@@ -144,7 +144,7 @@ k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const
         const int64_t col = rc.c0 + tid;
         const bool act = col < rc.dlo;
         uint32_t tlo = 0;
-        if (act) tlo = FULL ? (uint32_t)col : __ldg(v.list_lo + v.list_lo_off[v.klo[rc.blk]] + col);
+        if (act) tlo = FULL ? (uint32_t)col : __ldg(v.list_lo + v.lst_lo_off[rc.blk] + col);
         const uint32_t shi = rc.thi ^ xhi, slo = tlo ^ xlo;
         const uint64_t s = (uint64_t)slo | ((uint64_t)shi << v.n_lo);
         R fr = R(0), fi = R(0);

@@ -117,7 +117,7 @@ __device__ __forceinline__ RowCtx decode_row(const SectorView &v, const Geom &ge
         rc.thi = (uint32_t)rowi;
         rc.own_base = rowi << v.n_lo;
     } else {
-        rc.thi = v.list_hi[v.list_hi_off[v.khi[b]] + rowi];
+        rc.thi = v.list_hi[v.lst_hi_off[b] + rowi];
         rc.own_base = v.off[b] + rowi * v.dlo[b];
     }
     return rc;
@@ -218,8 +218,24 @@ template <> struct ExpAcc<float> {
 // KFULL: full space; KBLK1 / KBLKN: one / several product blocks, source rows
 // staged by bit pattern (2^n_lo slots, zeros outside the block); KBLKR: one
 // product block, source rows staged densely by rank and found through a rank
-// table in shared memory (for splits too wide for 2^n_lo slots).
-enum : int { KFULL = 0, KBLK1 = 1, KBLKN = 2, KBLKR = 3 };
+// table in shared memory (for splits too wide for 2^n_lo slots); KBLKC: KBLKN
+// for point-group sectors, whose blocks are (popcount, irrep) classes.  Only
+// KBLKC and KBLKR evaluate the class of a half-string (KBLKR once per row and
+// rank table); the popcount kinds keep one POPC in their inner loops.
+enum : int { KFULL = 0, KBLK1 = 1, KBLKN = 2, KBLKR = 3, KBLKC = 4 };
+
+__host__ __device__ constexpr bool kind_multi(int k) { return k == KBLKN || k == KBLKC; }
+
+template <int KIND>
+__device__ __forceinline__ int kcls_lo(const SectorView &v, uint32_t s) {
+    if constexpr (KIND == KBLKC || KIND == KBLKR) return cls_lo(v, s);
+    else return __popc(s);
+}
+template <int KIND>
+__device__ __forceinline__ int kcls_hi(const SectorView &v, uint32_t s) {
+    if constexpr (KIND == KBLKC || KIND == KBLKR) return cls_hi(v, s);
+    else return __popc(s);
+}
 
 // Rank table of KBLKR: n_lo <= 14: u16 lut[2^n_lo] (D_lo, the zero slot, for
 // strings outside the block); 15..16: u32 tabA[256] (colex rank of the low
@@ -274,12 +290,14 @@ __device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &
     int64_t base;
     int64_t len;
     int klo = 0;
+    int64_t loff = 0;
     if (KIND == KFULL) {
         base = (int64_t)shi << v.n_lo;
         len = 1ll << v.n_lo;
     } else {
-        const int bb = v.blk_of_khi[cls_hi(v, shi)];
+        const int bb = v.blk_of_khi[kcls_hi<KIND>(v, shi)];
         klo = v.klo[bb];
+        loff = v.lst_lo_off[bb];
         base = v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
         len = v.dlo[bb];
     }
@@ -297,7 +315,7 @@ __device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &
             else cp_async8(B.row + r, psi + base + r);
         }
     } else {
-        const uint32_t *lst = v.list_lo + v.list_lo_off[klo];
+        const uint32_t *lst = v.list_lo + loff;
         for (int64_t r = tid; r < len; r += nth) {
             const uint32_t pos = __ldg(lst + r);
             if (sizeof(C2) == 16) cp_async16(B.row + pos, psi + base + r);
@@ -345,7 +363,7 @@ __device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &
         if (sizeof(R) == 4) B.alo[s - sbase] = lo;
         B.z[s - sbase] = __ldg(p.s_zlo + s);
     }
-    if (KIND == KBLKN && tid == 0) *klo_req = klo;
+    if (kind_multi(KIND) && tid == 0) *klo_req = klo;
 }
 
 template <typename R, int KIND>
@@ -353,7 +371,7 @@ __device__ __forceinline__ int next_piece(const SectorView &v, const PlanDev &p,
     for (++q; q < pend; ++q) {
         if (KIND == KFULL) break;
         const uint32_t shi = thi ^ __ldg(p.pc_xhi + q);
-        if (v.blk_of_khi[cls_hi(v, shi)] >= 0) break;
+        if (v.blk_of_khi[kcls_hi<KIND>(v, shi)] >= 0) break;
     }
     return q;
 }
@@ -442,7 +460,7 @@ __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev 
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
             C2 amp = amp0[j];
-            if (KIND == KBLKN && cls_lo(v, s[j]) != klo_req) {
+            if (kind_multi(KIND) && kcls_lo<KIND>(v, s[j]) != klo_req) {
                 amp.x = R(0);
                 amp.y = R(0);
             }
@@ -473,7 +491,7 @@ __device__ __forceinline__ void lofree_piece(const SectorView &v, const PlanDev 
     if (KIND == KFULL) {
         base = (int64_t)shi << v.n_lo;
     } else {
-        const int bb = v.blk_of_khi[cls_hi(v, shi)];
+        const int bb = v.blk_of_khi[kcls_hi<KIND>(v, shi)];
         base = v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
     }
     C2 amp[TPT];
@@ -584,7 +602,7 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
         const int64_t c = rc.c0 + tid + j * kThreads;
         act[j] = c < rc.dlo;
         tlo[j] = 0;
-        if (act[j]) tlo[j] = (KIND == KFULL) ? (uint32_t)c : __ldg(v.list_lo + v.list_lo_off[v.klo[rc.blk]] + c);
+        if (act[j]) tlo[j] = (KIND == KFULL) ? (uint32_t)c : __ldg(v.list_lo + v.lst_lo_off[rc.blk] + c);
         accr[j] = R(0);
         acci[j] = R(0);
     }
@@ -611,7 +629,7 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
         }
     } else {
         while (q < pend) {
-            if (KIND != KBLKN && __ldg(p.pc_lofree + q)) {
+            if (!kind_multi(KIND) && __ldg(p.pc_lofree + q)) {
                 lofree_piece<R, KIND, REALH, TPT>(v, p, q, rc.thi, psi, rc.c0, act, tlo, accr, acci);
             } else {
                 stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
@@ -665,11 +683,12 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
     }
 }
 
-// FP32 path: register budget of four resident CTAs (64 registers a thread),
-// the allocation measured fastest on the 24-qubit molecule (the compiler's own
-// choice for this body spills); the FP64 path keeps the compiler's choice.
+// Four or more FP32 columns a thread: a register budget of four resident CTAs
+// (64 registers a thread), which the compiler picks by itself for a real
+// operator and otherwise undershoots with spills; every other instantiation
+// keeps the compiler's own allocation.
 template <typename R, int KIND, bool REALH, int TPT, int NBUF>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && TPT >= 4) ? 4 : 1)
 k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
         typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
     extern __shared__ __align__(16) char smem[];
@@ -805,7 +824,7 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
             e.klo = 0;
             e.base = (int64_t)shi << v.n_lo;
         } else {
-            const int bb = v.blk_of_khi[cls_hi(v, shi)];
+            const int bb = v.blk_of_khi[kcls_hi<KIND>(v, shi)];
             e.klo = bb < 0 ? -1 : v.klo[bb];
             e.base = bb < 0 ? 0 : v.off[bb] + (int64_t)__ldg(v.rank_hi + shi) * v.dlo[bb];
         }
@@ -855,7 +874,7 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
         const int64_t c = rc.c0 + tid + j * kThreads;
         act[j] = c < rc.dlo;
         tlo[j] = 0;
-        if (act[j]) tlo[j] = (KIND == KFULL) ? (uint32_t)c : __ldg(v.list_lo + v.list_lo_off[v.klo[rc.blk]] + c);
+        if (act[j]) tlo[j] = (KIND == KFULL) ? (uint32_t)c : __ldg(v.list_lo + v.lst_lo_off[rc.blk] + c);
         accr[j] = R(0);
         acci[j] = R(0);
     }
@@ -887,7 +906,7 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
                 s[j] = tlo[j] ^ e.xlo;
-                const bool ok = act[j] && (cls_lo(v, s[j]) == e.klo);
+                const bool ok = act[j] && (kcls_lo<KIND>(v, s[j]) == e.klo);
                 const int64_t idx = e.base + (ok ? (int64_t)__ldg(v.rank_lo + s[j]) : 0);
                 amp[j] = psi[idx];
                 if (!ok) {
@@ -1216,7 +1235,10 @@ void launch_apply_prec(const ApplyCfg &cfg, const Plan &p, const SectorView &v, 
     using C2 = typename Cx<R>::T;
     const Geom geo = make_geom(v, cfg.tpt * kThreads, cfg.nsplit, cfg.split_p0.data(), (int32_t)p.P);
     const PlanDev pd = plan_dev(p);
-    const int kind = v.kind == PAULI_SECTOR_FULL ? KFULL : (v.nblk == 1 ? (cfg.ranked ? KBLKR : KBLK1) : KBLKN);
+    const int kind = v.kind == PAULI_SECTOR_FULL ? KFULL
+                     : (v.nblk == 1 && cfg.ranked) ? KBLKR
+                     : v.irr ? KBLKC
+                     : v.nblk == 1 ? KBLK1 : KBLKN;
     void *kout = out;
     int flags = (out ? 1 : 0) | (partials ? 2 : 0);
     if (cfg.nsplit > 1) {
@@ -1227,12 +1249,14 @@ void launch_apply_prec(const ApplyCfg &cfg, const Plan &p, const SectorView &v, 
         if (kind == KFULL) launch_kind<R, KFULL, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
         else if (kind == KBLK1) launch_kind<R, KBLK1, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
         else if (kind == KBLKR) launch_kind<R, KBLKR, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
-        else launch_kind<R, KBLKN, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else if (kind == KBLKN) launch_kind<R, KBLKN, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else launch_kind<R, KBLKC, true>(cfg, v, geo, pd, in, kout, partials, flags, st);
     } else {
         if (kind == KFULL) launch_kind<R, KFULL, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
         else if (kind == KBLK1) launch_kind<R, KBLK1, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
         else if (kind == KBLKR) launch_kind<R, KBLKR, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
-        else launch_kind<R, KBLKN, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else if (kind == KBLKN) launch_kind<R, KBLKN, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
+        else launch_kind<R, KBLKC, false>(cfg, v, geo, pd, in, kout, partials, flags, st);
     }
     if (cfg.nsplit > 1) {
         const int cflags = (out ? 1 : 0) | (partials ? 2 : 0);

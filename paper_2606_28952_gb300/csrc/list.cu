@@ -435,7 +435,7 @@ void build_lists(const Allocator &al, Plan &p, const SectorView &v, cudaStream_t
     const int64_t dlo = v.dlo[0];
     std::vector<uint32_t> pat(dlo > 0 ? dlo : 1);
     if (dlo > 0)
-        PS_CUDA(cudaMemcpyAsync(pat.data(), v.list_lo + v.list_lo_off[klo], dlo * sizeof(uint32_t),
+        PS_CUDA(cudaMemcpyAsync(pat.data(), v.list_lo + v.lst_lo_off[0], dlo * sizeof(uint32_t),
                                 cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     std::vector<int32_t> rank(1u << n_lo, -1);

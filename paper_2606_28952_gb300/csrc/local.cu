@@ -57,11 +57,19 @@ __device__ __forceinline__ double2 ld_tab<double>(const LocalArgs &a, uint32_t l
     return __ldg(a.dtab64 + l);
 }
 
+// acc += f a for a real f: one packed FP32x2 FMA on the complex64 path
+__device__ __forceinline__ void acc_real(float2 &acc, float f, float2 a) { acc = __ffma2_rn(make_float2(f, f), a, acc); }
+__device__ __forceinline__ void acc_real(double2 &acc, double f, double2 a) {
+    acc.x = fma(f, a.x, acc.x);
+    acc.y = fma(f, a.y, acc.y);
+}
+
 template <typename R, bool REALH, int TPT>
 __global__ void __launch_bounds__(kThreads)
 k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__ psi,
               typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
     using C2 = typename Cx<R>::T;
+    constexpr int kEShift = sizeof(C2) == 8 ? 3 : 4;  // log2 of the amplitude size
     extern __shared__ __align__(16) char smem[];
     const int nloc = 1 << P.b;
     const int ng = P.g1 - P.g0;
@@ -101,7 +109,9 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
         cv.x = (R)(neg ? -c.x : c.x);
         cv.y = (R)(neg ? -c.y : c.y);
         sm_c[t] = cv;
-        sm_z[t] = __ldg(A.t_zloc + tt);
+        // Z masks in byte-offset units of the chunk (popcount(z << k & s << k) =
+        // popcount(z & s)), so sources are addressed without a multiply
+        sm_z[t] = __ldg(A.t_zloc + tt) << kEShift;
     }
     for (int g = tid; g < ng; g += kThreads) {
         const int gg = P.g0 + g;
@@ -155,7 +165,7 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
                 const C2 c = sm_c[t];
 #pragma unroll
                 for (int j = 0; j < TPT; ++j) {
-                    const uint32_t par = __popc(z & tl[j]);
+                    const uint32_t par = __popc(z & (tl[j] << kEShift));
                     fr[j] += flip(c.x, par);
                     if (!REALH) fi[j] += flip(c.y, par);
                 }
@@ -180,14 +190,37 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
                 acci[j] = R(0);
             }
         }
+        const char *cb = reinterpret_cast<const char *>(chunk);
+        uint32_t tb[TPT];  // byte offsets of the targets in the chunk
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) tb[j] = tl[j] << kEShift;
+        C2 acc2[TPT];
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            acc2[j].x = accr[j];
+            acc2[j].y = acci[j];
+        }
         for (int g = g_start; g < ng; ++g) {
             const int4 gr = sm_g[g];
             const C2 a0 = sm_a0[g];
+            const uint32_t xb = (uint32_t)gr.x << kEShift;
+            if (REALH && gr.z - gr.y == 1) {
+                // one term besides the folded z_loc = 0 ones (a lattice bond: XX + YY)
+                const uint32_t z = sm_z[gr.y];
+                const R c = sm_c[gr.y].x;
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) {
+                    const uint32_t sb = tb[j] ^ xb;
+                    const R f = a0.x + flip(c, __popc(z & sb));
+                    acc_real(acc2[j], f, *reinterpret_cast<const C2 *>(cb + sb));
+                }
+                continue;
+            }
             R fr[TPT], fi[TPT];
-            uint32_t s[TPT];
+            uint32_t sb[TPT];
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
-                s[j] = tl[j] ^ (uint32_t)gr.x;
+                sb[j] = tb[j] ^ xb;
                 fr[j] = a0.x;
                 if (!REALH) fi[j] = a0.y;
             }
@@ -196,22 +229,26 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
                 const C2 c = sm_c[t];
 #pragma unroll
                 for (int j = 0; j < TPT; ++j) {
-                    const uint32_t par = __popc(z & s[j]);
+                    const uint32_t par = __popc(z & sb[j]);
                     fr[j] += flip(c.x, par);
                     if (!REALH) fi[j] += flip(c.y, par);
                 }
             }
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
-                const C2 amp = chunk[s[j]];
+                const C2 amp = *reinterpret_cast<const C2 *>(cb + sb[j]);
                 if (REALH) {
-                    accr[j] += fr[j] * amp.x;
-                    acci[j] += fr[j] * amp.y;
+                    acc_real(acc2[j], fr[j], amp);
                 } else {
-                    accr[j] += fr[j] * amp.x - fi[j] * amp.y;
-                    acci[j] += fr[j] * amp.y + fi[j] * amp.x;
+                    acc2[j].x += fr[j] * amp.x - fi[j] * amp.y;
+                    acc2[j].y += fr[j] * amp.y + fi[j] * amp.x;
                 }
             }
+        }
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            accr[j] = acc2[j].x;
+            acci[j] = acc2[j].y;
         }
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {

@@ -107,13 +107,15 @@ struct SectorView {
     int64_t off[kMaxBlocks + 1];      // first index of each block
     int64_t dlo[kMaxBlocks], dhi[kMaxBlocks];
     int64_t row_off[kMaxBlocks + 1];  // first row of each block
-    int blk_of_khi[kMaxCls];          // class of the high half -> block or -1
+    int64_t lst_lo_off[kMaxBlocks];   // first entry of each block's low class in list_lo
+    int64_t lst_hi_off[kMaxBlocks];   // ... and of its high class in list_hi
     const uint32_t *rank_lo;          // [2^n_lo] rank inside the string's class
     const uint32_t *rank_hi;          // [2^n_hi]
     const uint32_t *list_lo;          // [2^n_lo] strings ordered by (class, value)
     const uint32_t *list_hi;          // [2^n_hi]
-    int64_t list_lo_off[kMaxCls + 1];  // first entry of each class in list_lo
-    int64_t list_hi_off[kMaxCls + 1];
+    int8_t blk_of_khi[kMaxCls];       // class of the high half -> block or -1
+    // (a kernel argument: kept to about 2 KB, every field read from the
+    //  constant bank by every CTA)
 };
 
 __host__ __device__ __forceinline__ int ps_popc32(uint32_t v) {

@@ -37,13 +37,20 @@ namespace {
 enum : int { RS_ROW = 0, RS_COL = 1, RS_PAIR = 2, RS_EACH = 3 };
 constexpr int kSeqThreads = 512;
 
+constexpr int kMaxActive = 4;   // active pair patterns kept per generator
+
 struct SeqGen {
     uint64_t x;
+    uint64_t m;                 // support S of the active test (np > 0)
+    uint64_t zo;                // Z bits common to every term outside S (np > 0)
+    uint64_t pat[kMaxActive];   // t & S of every target whose pair rotates (np of them)
+    double2 F[kMaxActive];      // f on each active pattern up to the sign (-1)^{zo . s}
     int t0, t1;    // terms of the generator in the sequence's term arrays
     int theta;     // index into the angle array
     int b0;        // lowest set bit of x (-1 for x = 0)
-    int *status;   // the generator's device status word (sector leaks)
+    int np;        // number of active patterns; 0: every pair representative is evaluated
     int pad;
+    int *status;   // the generator's device status word (sector leaks)
 };
 
 struct SeqArgs {
@@ -53,7 +60,7 @@ struct SeqArgs {
     const double2 *tc;          // [terms] XZ-form coefficients
     const double *theta;        // [K] angles (device)
     uint64_t xh;                // PAIR: the run's common x_hi
-    int width;                  // COL: columns per tile
+    int lw;                     // COL: log2 of the columns per tile
     int has_local;              // PAIR: a generator of the run acts inside one row
 };
 
@@ -71,25 +78,41 @@ template <typename R> __device__ __forceinline__ void sincos_s(R a, R *s, R *c);
 template <> __device__ __forceinline__ void sincos_s<float>(float a, float *s, float *c) { sincosf(a, s, c); }
 template <> __device__ __forceinline__ void sincos_s<double>(double a, double *s, double *c) { sincos(a, s, c); }
 
+// Entry e of a tile: row rs, column cc (ROW: one row; PAIR: two rows of ld
+// columns; COL: rows of 2^lw columns).
+template <int MODE>
+__device__ __forceinline__ void seq_entry(int e, int ld, int lw, int &rs, int &cc) {
+    if (MODE == RS_ROW) {
+        rs = 0;
+        cc = e;
+    } else if (MODE == RS_PAIR) {
+        rs = e >= ld;
+        cc = e - rs * ld;
+    } else {
+        rs = e >> lw;
+        cc = e & ((1 << lw) - 1);
+    }
+}
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kSeqThreads)
 k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
     using C2 = typename Cx<R>::T;
     extern __shared__ __align__(16) char smem[];
-    C2 *tile = reinterpret_cast<C2 *>(smem);
     const int tid = threadIdx.x;
     const int klo = v.klo[0], khi = v.khi[0];
     const int64_t dlo = v.dlo[0], off = v.off[0];
-    const uint32_t *lst_lo = v.list_lo + v.list_lo_off[klo];
-    const uint32_t *lst_hi = v.list_hi + v.list_hi_off[khi];
-    const uint32_t lomask = (uint32_t)((1ull << v.n_lo) - 1ull);
-    int nrow = 1;
-    int64_t ncol = dlo, c0 = 0;
-    uint32_t rpat[2] = {0u, 0u};
+    const uint32_t *lst_lo = v.list_lo + v.lst_lo_off[0];
+    const uint32_t *lst_hi = v.list_hi + v.lst_hi_off[0];
+    const uint64_t lomask = (1ull << v.n_lo) - 1ull;
+    int nrow = 1, ld = (int)dlo, ncol = (int)dlo;
+    int64_t c0 = 0;
     int64_t rrank[2] = {0, 0};
+    uint32_t rpat[2] = {0u, 0u};
     if (MODE == RS_COL) {
-        c0 = (int64_t)blockIdx.x * A.width;
-        ncol = min((int64_t)A.width, dlo - c0);
+        ld = 1 << A.lw;
+        c0 = (int64_t)blockIdx.x * ld;
+        ncol = (int)min((int64_t)ld, dlo - c0);
         nrow = (int)v.dhi[0];
     } else {
         const int64_t i = blockIdx.x;
@@ -108,27 +131,57 @@ k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
             }
         }
     }
-    const int64_t nent = (int64_t)nrow * ncol;
-    // 1. the tile -> shared memory (rows are contiguous runs of ncol amplitudes)
-    for (int64_t e = tid; e < nent; e += kSeqThreads) {
-        const int64_t rs = e / ncol, cc = e - rs * ncol;
+    C2 *tile = reinterpret_cast<C2 *>(smem);
+    uint32_t *tlo_s = reinterpret_cast<uint32_t *>(smem + (size_t)nrow * ld * sizeof(C2));
+    uint32_t *thi_s = tlo_s + ld;
+    const int nent = nrow * ld;
+    // 1. the tile -> shared memory (rows are contiguous runs of ncol amplitudes),
+    //    with the strings of its rows and columns
+    for (int c = tid; c < ncol; c += kSeqThreads) tlo_s[c] = __ldg(lst_lo + c0 + c);
+    for (int r = tid; r < nrow; r += kSeqThreads) thi_s[r] = (MODE == RS_COL) ? __ldg(lst_hi + r) : rpat[r];
+    for (int e = tid; e < nent; e += kSeqThreads) {
+        int rs, cc;
+        seq_entry<MODE>(e, ld, A.lw, rs, cc);
+        if (cc >= ncol) continue;
         const int64_t rowrank = (MODE == RS_COL) ? rs : rrank[rs];
         tile[e] = psi[off + rowrank * dlo + c0 + cc];
     }
     __syncthreads();
-    // 2. the run's rotations, in order
+    // 2. the run's rotations, in order; a target is skipped unless its pair can
+    //    rotate (its pattern on the generator's support is active)
     for (int gi = A.g0; gi < A.g1; ++gi) {
-        const SeqGen g = A.gens[gi];
+        const SeqGen &g = A.gens[gi];
+        const uint64_t gx = g.x, gm = g.m;
+        const int np = g.np, b0 = g.b0;
+        uint64_t pat[kMaxActive];
+#pragma unroll
+        for (int k = 0; k < kMaxActive; ++k) pat[k] = g.pat[k];
         const R theta = (R)__ldg(A.theta + g.theta);
-        for (int64_t e = tid; e < nent; e += kSeqThreads) {
-            const int64_t rs = e / ncol, cc = e - rs * ncol;
-            const uint32_t thi = (MODE == RS_COL) ? __ldg(lst_hi + rs) : rpat[rs];
-            const uint32_t tlo = __ldg(lst_lo + c0 + cc);
+        for (int e = tid; e < nent; e += kSeqThreads) {
+            int rs, cc;
+            seq_entry<MODE>(e, ld, A.lw, rs, cc);
+            if (cc >= ncol) continue;
+            const uint32_t thi = thi_s[rs], tlo = tlo_s[cc];
             const uint64_t t = (uint64_t)tlo | ((uint64_t)thi << v.n_lo);
+            const uint64_t s = t ^ gx;   // the pair partner (t itself for a diagonal generator)
             R fr = R(0), fi = R(0);
-            if (g.x == 0) {
+            if (np != 0) {
+                const uint64_t tm = t & gm;
+                int kk = -1;
+#pragma unroll
+                for (int k = 0; k < kMaxActive; ++k)
+                    if (k < np && tm == pat[k]) kk = k;
+                if (kk < 0) continue;
+                const double2 F = g.F[kk];
+                const uint32_t par = __popcll(g.zo & s);
+                fr = flip((R)F.x, par);
+                fi = flip((R)F.y, par);
+            } else {
+                if (gx != 0 && !((t >> b0) & 1ull)) continue;  // each pair from its member with bit b0 set
+                phase_sum<R>(A, g, s, fr, fi);
+            }
+            if (gx == 0) {
                 // exp(-i theta f_t) on one amplitude (f real for a Hermitian diagonal generator)
-                phase_sum<R>(A, g, t, fr, fi);
                 R sn, cs;
                 sincos_s<R>(theta * fr, &sn, &cs);
                 const C2 a = tile[e];
@@ -138,20 +191,17 @@ k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
                 tile[e] = o;
                 continue;
             }
-            if (!((t >> g.b0) & 1ull)) continue;  // each pair from its member with bit b0 set
-            const uint64_t s = t ^ g.x;
             const uint32_t slo = (uint32_t)(s & lomask), shi = (uint32_t)(s >> v.n_lo);
-            phase_sum<R>(A, g, s, fr, fi);
             bool in = cls_lo(v, slo) == klo && cls_hi(v, shi) == khi;
-            int64_t pe = 0;
+            int pe = 0;
             if (in) {
                 if (MODE == RS_COL) {
-                    pe = (int64_t)__ldg(v.rank_hi + shi) * ncol + cc;
+                    pe = ((int)__ldg(v.rank_hi + shi) << A.lw) + cc;
                 } else {
-                    int64_t prs = rs;
+                    int prs = rs;
                     if (shi != thi) prs = (nrow == 2 && shi == rpat[rs ^ 1]) ? (rs ^ 1) : -1;
                     if (prs < 0) in = false;
-                    else pe = prs * ncol + (int64_t)__ldg(v.rank_lo + slo);
+                    else pe = prs * ld + (int)__ldg(v.rank_lo + slo);
                 }
             }
             if (!in) {
@@ -177,8 +227,10 @@ k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
         __syncthreads();
     }
     // 3. the tile -> psi
-    for (int64_t e = tid; e < nent; e += kSeqThreads) {
-        const int64_t rs = e / ncol, cc = e - rs * ncol;
+    for (int e = tid; e < nent; e += kSeqThreads) {
+        int rs, cc;
+        seq_entry<MODE>(e, ld, A.lw, rs, cc);
+        if (cc >= ncol) continue;
         const int64_t rowrank = (MODE == RS_COL) ? rs : rrank[rs];
         psi[off + rowrank * dlo + c0 + cc] = tile[e];
     }
@@ -222,18 +274,78 @@ void free_seq(pauli_rotseq *q) {
     delete q;
 }
 
-// columns of a COL tile: 64-byte row segments, fewer if every row does not fit
-int64_t col_width(const SectorView &v, size_t es) {
-    const int64_t want = (int64_t)(64 / es);
-    const int64_t fit = (int64_t)(226 * 1024 / (es * (size_t)std::max<int64_t>(1, v.dhi[0])));
-    return std::min<int64_t>({want, fit, v.dlo[0]});
+// Shared memory of one tile: nrow x ld amplitudes, the low strings of its
+// columns (u32 [ld]) and the high strings of its rows (u32 [nrow]).
+size_t tile_bytes(int64_t nrow, int64_t ld, size_t es) {
+    return (size_t)nrow * (size_t)ld * es + (size_t)ld * 4 + (size_t)nrow * 4;
+}
+
+// log2 of the columns of a COL tile: 32-byte row segments, halved while the
+// grid would hold fewer than two tiles per SM or the tile does not fit
+int col_lw(const SectorView &v, size_t es) {
+    int lw = es == 8 ? 2 : 1;
+    const int64_t want = 2 * (int64_t)num_sms();
+    while (lw > 0 && ((v.dlo[0] + (1ll << lw) - 1) >> lw) < want) --lw;
+    while (lw > 0 && tile_bytes(v.dhi[0], 1ll << lw, es) > 226 * 1024) --lw;
+    return lw;
+}
+
+// Active pairs of one generator.  With D = OR_k (z_k ^ z_0), S = x | D and
+// z_o = z_0 & ~S, f(s) = sum_k c_k (-1)^{z_k . s} = (-1)^{z_o . s} F(s & S),
+// F(r) = sum_k c_k (-1)^{z_k . r} (every term has the same Z bits outside S).
+// Whether a pair {t, t ^ x} rotates, and by how much, depends only on the
+// target's pattern q = t & S; every q that represents a pair (bit b0 of x set;
+// every q when x is 0) with F(q ^ x) != 0 is kept, with F(q ^ x) summed in the
+// order of the terms (the order of the per-target sum, so the complex128 values
+// are the same bits), when S has at most 14 bits and at most kMaxActive
+// patterns are active (np = -1: none is; np = 0: the test is off and every
+// representative sums its terms).
+void active_patterns(SeqGen &g, const std::vector<uint64_t> &hz, const std::vector<double2> &hc) {
+    g.np = 0;
+    g.m = 0;
+    g.zo = 0;
+    for (int k = 0; k < kMaxActive; ++k) {
+        g.pat[k] = 0;
+        g.F[k] = make_double2(0.0, 0.0);
+    }
+    if (hz.empty()) return;
+    uint64_t d = 0;
+    for (uint64_t z : hz) d |= z ^ hz[0];
+    const uint64_t S = g.x | d;
+    if (__builtin_popcountll(S) > 14) return;
+    std::vector<uint64_t> act;
+    std::vector<double2> fval;
+    uint64_t q = 0;
+    do {
+        if (g.x == 0 || ((q >> g.b0) & 1ull)) {
+            const uint64_t sq = q ^ g.x;
+            double fr = 0.0, fi = 0.0;
+            for (size_t t = 0; t < hz.size(); ++t) {
+                const bool odd = __builtin_popcountll(hz[t] & sq) & 1;
+                fr += odd ? -hc[t].x : hc[t].x;
+                fi += odd ? -hc[t].y : hc[t].y;
+            }
+            if (fr != 0.0 || fi != 0.0) {
+                act.push_back(q);
+                fval.push_back(make_double2(fr, fi));
+                if ((int)act.size() > kMaxActive) return;
+            }
+        }
+        q = (q - S) & S;  // next subset of S
+    } while (q != 0);
+    g.m = S;
+    g.zo = hz[0] & ~S;
+    g.np = act.empty() ? -1 : (int)act.size();
+    for (size_t k = 0; k < act.size(); ++k) {
+        g.pat[k] = act[k];
+        g.F[k] = fval[k];
+    }
 }
 
 size_t run_smem(const pauli_rotseq::Run &r, const SectorView &v, size_t es) {
-    if (r.mode == RS_ROW) return (size_t)v.dlo[0] * es;
-    if (r.mode == RS_PAIR) return 2 * (size_t)v.dlo[0] * es;
-    const int64_t w = col_width(v, es);
-    return w < 1 ? SIZE_MAX : (size_t)v.dhi[0] * (size_t)w * es;
+    if (r.mode == RS_ROW) return tile_bytes(1, v.dlo[0], es);
+    if (r.mode == RS_PAIR) return tile_bytes(2, v.dlo[0], es);
+    return tile_bytes(v.dhi[0], 1ll << col_lw(v, es), es);
 }
 
 template <typename R>
@@ -249,7 +361,7 @@ void launch_run(const pauli_rotseq *q, const pauli_rotseq::Run &r, void *psi, cu
     A.tc = q->d_tc;
     A.theta = q->d_theta;
     A.xh = r.xh;
-    A.width = (int)col_width(v, es);
+    A.lw = col_lw(v, es);
     A.has_local = r.has_local;
     const size_t smem = run_smem(r, v, es);
     C2 *p = static_cast<C2 *>(psi);
@@ -262,7 +374,7 @@ void launch_run(const pauli_rotseq *q, const pauli_rotseq::Run &r, void *psi, cu
     };
     if (r.mode == RS_ROW) go(k_rotseq<R, RS_ROW>, v.dhi[0]);
     else if (r.mode == RS_PAIR) go(k_rotseq<R, RS_PAIR>, v.dhi[0]);
-    else go(k_rotseq<R, RS_COL>, (v.dlo[0] + A.width - 1) / A.width);
+    else go(k_rotseq<R, RS_COL>, (v.dlo[0] + (1ll << A.lw) - 1) >> A.lw);
 }
 
 }  // namespace
@@ -321,6 +433,7 @@ int pauli_rotseq_create(pauli_sum *const *Gs, int K, const pauli_sector *s, paul
             g.b0 = x ? __builtin_ctzll(x) : -1;
             g.status = G->status;
             g.pad = 0;
+            active_patterns(g, hz, hc);
             gen_of.push_back((int)gens.size());
             gens.push_back(g);
         }

@@ -106,8 +106,8 @@ __global__ void k_sector_unrank(SectorView v, const int64_t *idx, int64_t n, uin
     uint64_t rlo = (uint64_t)(rem % v.dlo[blk]);
     uint32_t hi, lo;
     if (v.irr) {
-        hi = v.list_hi[v.list_hi_off[v.khi[blk]] + rhi];
-        lo = v.list_lo[v.list_lo_off[v.klo[blk]] + rlo];
+        hi = v.list_hi[v.lst_hi_off[blk] + rhi];
+        lo = v.list_lo[v.lst_lo_off[blk] + rlo];
     } else {
         hi = colex_unrank(v.n_hi, v.khi[blk], rhi);
         lo = colex_unrank(v.n_lo, v.klo[blk], rlo);
@@ -141,7 +141,7 @@ void build_sector_tables(pauli_sector *s, cudaStream_t st) {
         for (int half = 0; half < 2; ++half) {
             const int bits = half ? v.n_hi : v.n_lo;
             const uint32_t *m = half ? v.irr_hi : v.irr_lo;
-            int64_t *off = half ? v.list_hi_off : v.list_lo_off;
+            std::vector<int64_t> off(kMaxCls + 1, 0);
             const int64_t cnt = 1ll << bits;
             std::vector<uint32_t> rk(cnt), ls(cnt);
             std::vector<int64_t> count(kMaxCls + 1, 0);
@@ -152,6 +152,7 @@ void build_sector_tables(pauli_sector *s, cudaStream_t st) {
             PS_CUDA(cudaMemcpyAsync(half ? rank_hi : rank_lo, rk.data(), cnt * 4, cudaMemcpyHostToDevice, st));
             PS_CUDA(cudaMemcpyAsync(half ? list_hi : list_lo, ls.data(), cnt * 4, cudaMemcpyHostToDevice, st));
             PS_CUDA(cudaStreamSynchronize(st));
+            for (int r = 0; r < v.nblk; ++r) (half ? v.lst_hi_off : v.lst_lo_off)[r] = off[half ? v.khi[r] : v.klo[r]];
         }
         v.rank_lo = rank_lo;
         v.list_lo = list_lo;
@@ -161,11 +162,11 @@ void build_sector_tables(pauli_sector *s, cudaStream_t st) {
     }
     for (int half = 0; half < 2; ++half) {
         const int bits = half ? v.n_hi : v.n_lo;
-        int64_t *off = half ? v.list_hi_off : v.list_lo_off;
-        off[0] = 0;
+        std::vector<int64_t> off(bits + 2, 0);
         for (int k = 0; k <= bits; ++k) off[k + 1] = off[k] + (int64_t)binom_host(bits, k);
+        for (int r = 0; r < v.nblk; ++r) (half ? v.lst_hi_off : v.lst_lo_off)[r] = off[half ? v.khi[r] : v.klo[r]];
         DevBuf<int64_t> d_off(s->al, bits + 2);
-        PS_CUDA(cudaMemcpyAsync(d_off.p, off, (bits + 2) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        PS_CUDA(cudaMemcpyAsync(d_off.p, off.data(), (bits + 2) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         uint32_t *rk = half ? rank_hi : rank_lo;
         uint32_t *ls = half ? list_hi : list_lo;
         const int64_t cnt = 1ll << bits;
@@ -247,7 +248,7 @@ void init_sector_view(SectorView &v, int n, int kind, int n_lo, int nb, const in
         v.row_off[r] = row;
         off += v.dlo[r] * v.dhi[r];
         row += v.dhi[r];
-        v.blk_of_khi[khi[r]] = r;
+        v.blk_of_khi[khi[r]] = (int8_t)r;
     }
     v.off[nb] = off;
     v.row_off[nb] = row;

@@ -198,7 +198,7 @@ k_apply_svd(SectorView v, Geom geo, SvdDev d, int pc0, int pc1, int64_t fa_row0,
     for (int j = 0; j < TPT; ++j) {
         col[j] = rc.c0 + tid + j * kThreads;
         act[j] = col[j] < rc.dlo;
-        tlo[j] = act[j] ? __ldg(v.list_lo + v.list_lo_off[klo] + col[j]) : 0u;
+        tlo[j] = act[j] ? __ldg(v.list_lo + v.lst_lo_off[0] + col[j]) : 0u;
         accr[j] = R(0);
         acci[j] = R(0);
     }
@@ -505,7 +505,7 @@ static void launch_svd_t(const ApplyCfg &cfg, const SvdPlan &sp, const SectorVie
     d.fa_g = sp.fa_g;
     d.fa_k = sp.fa_k;
     d.fa_diag = sp.fa_diag;
-    const uint32_t *lst_lo = v.list_lo + v.list_lo_off[v.klo[0]];
+    const uint32_t *lst_lo = v.list_lo + v.lst_lo_off[0];
     const int nb = (int)sp.h_batch_pc0.size() - 1;
     const size_t smem = cfg.smem;
     auto kern = k_apply_svd<R, TPT>;

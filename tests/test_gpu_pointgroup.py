@@ -129,3 +129,40 @@ def test_pointgroup_rotations_sequences_and_pool(ps):
         g = P.gradients(torch.from_numpy(psi).cuda(), hp).cpu().numpy()
         gref = ovqe.pool_gradients(So, R, gens_or, psi)
         assert np.abs(g - gref).max() <= 1e-11 * max(1.0, np.abs(gref).max())
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_pointgroup_batch(ps, dt):
+    """Single-block irrep sectors in one batched launch, mixed with a plain
+    (popcount) molecular sector: every installed shape (uniform pattern or rank
+    staging, per-state groups) gives each state's H psi and <H> of the oracle."""
+    import torch
+    cases = [_case(ps, 6, 3, 3, 0, seed=s, single=True) for s in (3, 4)] + \
+            [_case(ps, 8, 4, 4, 3, seed=5, single=True)]
+    h, g = w.molecular_integrals(7, 2)
+    Hm = ps.PauliSum.jw_molecular(h, g, eps_drop=1e-12)
+    Rm = oracle.jw_hamiltonian(7, h, g, eps_drop=1e-12)
+    Sm, Smo = ps.Sector.molecular(7, 3, 4), oracle.Sector.molecular(7, 3, 4)
+    Hs = [c[0] for c in cases] + [Hm]
+    Rs = [c[1] for c in cases] + [Rm]
+    Ss = [c[2] for c in cases] + [Sm]
+    Sos = [c[3] for c in cases] + [Smo]
+    psis = [_rounded(w.random_state(S.dim, 90 + i), dt) for i, S in enumerate(Ss)]
+    refs = [oracle.apply(So, R, p) for So, R, p in zip(Sos, Rs, psis)]
+    Es = [oracle.expect(So, R, p)[0] for So, R, p in zip(Sos, Rs, psis)]
+    xs = [torch.from_numpy(p).to("cuda", _tdt(dt)) for p in psis]
+    outs = [torch.empty_like(x) for x in xs]
+    B = ps.Batch(Hs, Ss, dtype=_tdt(dt))
+    res = torch.empty((len(Ss), 4), dtype=torch.float64, device="cuda")
+    for shape in (None, ps.LaunchConfig(cols_per_thread=2, staged_rows=1, row_split=1, direct=0, ranked=0, ms=0.0),
+                  ps.LaunchConfig(cols_per_thread=0, staged_rows=1, row_split=1, direct=0, ranked=0, ms=0.0)):
+        if shape is not None:
+            B.set_launch_config(shape)
+        for o in outs:
+            o.zero_()
+        B.apply(xs, outs, res)
+        r = res.cpu().numpy()
+        for i in range(len(Ss)):
+            got = outs[i].cpu().numpy().astype(np.complex128)
+            assert np.linalg.norm(got - refs[i]) <= TOL[dt] * np.linalg.norm(refs[i]), (shape, i)
+            assert abs(complex(r[i, 0], r[i, 1]) - Es[i]) <= (1e-12 if dt == "c128" else 1e-6) * max(1.0, abs(Es[i]))
