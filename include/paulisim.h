@@ -283,6 +283,29 @@ int pauli_expect(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype
 int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype,
                          double *result, void *hpsi_out, pauli_stream_t st);
 
+/* Selected rows of H psi: the target-driven gather of eq. reverse_sum
+ * evaluated only at the n_rows target indices rows[0..n_rows) (DEVICE int64,
+ * sector indices in [0, dim), distinct), one CTA per target, every group of H
+ * in a fixed order.
+ *   hpsi_out (DEVICE state vector of dim entries, or NULL): entry rows[i]
+ *     <- (H psi)[rows[i]]; every other entry is left as it is.
+ *   result (DEVICE, 4 doubles, or NULL): { Re, Im of sum_i conj(psi[r_i])
+ *     (H psi)[r_i], sum_i |(H psi)[r_i]|^2, sum_i |psi[r_i]|^2 }, FP64 in a
+ *     fixed order.  When psi vanishes outside the listed rows (a state that
+ *     lives on a known set of configurations, e.g. the seniority-zero strings
+ *     a pair-double ansatz reaches from a closed-shell reference), result[0]
+ *     and result[1] are <psi|H|psi> exactly as pauli_expect gives them, and
+ *     hpsi_out holds the part of H psi on those rows (all that the adjoint
+ *     gradient of such a state needs).
+ * At least one of hpsi_out and result must be given.  Precision as
+ * pauli_apply (C64: FP32 group sums, C128: FP64).  An index outside [0, dim)
+ * is skipped (nothing read or written for it, zero partials) and sets H's
+ * device status word to PAULI_EINVAL (pauli_status).  The first call with
+ * result, and any call with more rows than before, allocates the operator's
+ * partial-sum buffer (n_rows x 4 doubles; synchronises st). */
+int pauli_expect_rows(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype, const int64_t *rows,
+                      int64_t n_rows, void *hpsi_out, double *result, pauli_stream_t st);
+
 /* psi <- exp(-i theta G) psi in place, for a Hermitian G with ONE X mask x
  * (a single group; Sec. 2.5 and the Trotter factors exp(theta tau) of
  * Sec. 3.2 with G = i tau).  G maps each pair {t, t XOR x} onto itself with

@@ -67,6 +67,7 @@ SIGNATURES = {
     "pauli_apply": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
     "pauli_expect": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "pauli_expect_noalloc": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "pauli_expect_rows": (_i32, [_vp, _vp, _vp, _i32, _vp, _i64, _vp, _vp, _vp]),
     "pauli_rotate": (_i32, [_vp, _vp, _dbl, _vp, _i32, _vp]),
     "pauli_rotate_seq": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "pauli_rotate_adjoint": (_i32, [_vp, _vp, _dbl, _vp, _vp, _i32, _vp, _vp]),
@@ -474,6 +475,28 @@ def expect(H: PauliSum, s: Sector, psi, hpsi_out=None, result=None, stream=None)
         hp = C.c_void_p(hpsi_out.data_ptr())
     _check(lib().pauli_expect(H._h, s._h, C.c_void_p(psi.data_ptr()), _dtype_code(psi),
                               C.c_void_p(result.data_ptr()), hp, _stream_ptr(stream)))
+    return result
+
+
+def expect_rows(H: PauliSum, s: Sector, psi, rows, hpsi_out=None, result=None, stream=None):
+    """Rows of H psi at the sector indices ``rows`` (device int64 tensor, distinct)
+    written into ``hpsi_out`` (a full-length state; other entries untouched), and
+    [Re, Im sum conj(psi_r) (H psi)_r, sum |(H psi)_r|^2, sum |psi_r|^2] over the
+    rows (device float64[4], returned).  <psi|H|psi> when psi vanishes off the rows."""
+    import torch
+    _check_state(psi, s.dim, "psi")
+    if not (isinstance(rows, torch.Tensor) and rows.dtype == torch.int64 and rows.is_cuda and rows.is_contiguous()
+            and rows.dim() == 1):
+        raise TypeError("rows: a contiguous 1-D int64 CUDA tensor")
+    if result is None:
+        result = torch.empty(4, dtype=torch.float64, device=psi.device)
+    hp = None
+    if hpsi_out is not None:
+        _check_state(hpsi_out, s.dim, "hpsi_out")
+        hp = C.c_void_p(hpsi_out.data_ptr())
+    _check(lib().pauli_expect_rows(H._h, s._h, C.c_void_p(psi.data_ptr()), _dtype_code(psi),
+                                   C.c_void_p(rows.data_ptr()), rows.numel(), hp, C.c_void_p(result.data_ptr()),
+                                   _stream_ptr(stream)))
     return result
 
 

@@ -202,6 +202,7 @@ void destroy_sum(pauli_sum *h) {
     dev_free(h->al, h->gx);
     dev_free(h->al, h->gstart);
     dev_free(h->al, h->status);
+    dev_free(h->al, h->rows_part);
     h->magic = 0;
     delete h;
 }
@@ -680,6 +681,42 @@ int pauli_expect(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype
                  "expect: the plan's partial-sum buffer is too small (internal)");
         launch_apply(H, p, s->v, psi, hpsi_out, dtype, p.partials, cs);
         launch_reduce(p.partials, nct, result, cs);
+    });
+}
+
+int pauli_expect_rows(pauli_sum *H, const pauli_sector *s, const void *psi, int dtype, const int64_t *rows,
+                      int64_t n_rows, void *hpsi_out, double *result, pauli_stream_t st) {
+    return guarded([&] {
+        check_sum(H);
+        check_sector(s);
+        check_dtype(dtype);
+        PS_CHECK(H->n == s->v.n, PAULI_EINVAL, "operator and sector have different qubit counts");
+        check_state_ptr(psi, dtype, "psi");
+        PS_CHECK(n_rows >= 0 && n_rows < (1ll << 31), PAULI_EINVAL, "n_rows must be in 0..2^31-1");
+        PS_CHECK(n_rows == 0 || rows != nullptr, PAULI_EINVAL, "rows is NULL");
+        PS_CHECK(hpsi_out != nullptr || result != nullptr, PAULI_EINVAL, "neither hpsi_out nor result is given");
+        if (hpsi_out) {
+            check_state_ptr(hpsi_out, dtype, "hpsi_out");
+            const size_t bytes = (size_t)s->v.dim * elem_size(dtype);
+            const char *a = static_cast<const char *>(psi);
+            const char *b = static_cast<const char *>(hpsi_out);
+            PS_CHECK(a + bytes <= b || b + bytes <= a, PAULI_EINVAL, "psi and hpsi_out overlap");
+        }
+        cudaStream_t cs = (cudaStream_t)st;
+        if (n_rows == 0) {
+            if (result) PS_CUDA(cudaMemsetAsync(result, 0, 4 * sizeof(double), cs));
+            return;
+        }
+        if (result && H->rows_cap < n_rows) {
+            PS_CUDA(cudaStreamSynchronize(cs));
+            dev_free(H->al, H->rows_part);
+            H->rows_part = nullptr;
+            H->rows_cap = 0;
+            H->rows_part = static_cast<double *>(dev_alloc(H->al, (size_t)n_rows * 4 * sizeof(double)));
+            H->rows_cap = n_rows;
+        }
+        launch_apply_rows(H, s->v, psi, rows, n_rows, hpsi_out, dtype, result ? H->rows_part : nullptr, cs);
+        if (result) launch_reduce(H->rows_part, n_rows, result, cs);
     });
 }
 

@@ -1,5 +1,6 @@
 // apply.cu -- dispatch of the gather kernels (apply_kernels.cuh), the fixed-order
 // FP64 reduction of pauli_expect and the single-group rotation kernel.
+#include <cmath>
 #include "apply_kernels.cuh"
 
 namespace ps {
@@ -250,11 +251,23 @@ k_rotate_adj(SectorView v, Geom geo, int64_t nwork, int64_t m, uint64_t x, const
 // The same rotation (ADJ: the adjoint step of k_rotate_adj) over the listed
 // pairs only (RotPairs): no work for targets whose partner leaves the block, and
 // each pair is visited once.  Fixed grid, block-strided over pair ids.
+// Angles of one rotation per active pattern (ActivePatterns), from the host:
+// f(s) = (-1)^{z_o . s} F_k for a target with t & S = pat[k], and
+// cos(theta |F_k|), sin(theta |F_k|) / |F_k| once per launch instead of per pair.
+template <typename R>
+struct RotAngles {
+    uint64_t S, zo;
+    uint64_t pat[kActMax];
+    R fr[kActMax], fi[kActMax];
+    R cs[kActMax], q[kActMax];
+    int np;  // 0: every pair sums its terms and takes its own sin / cos
+};
+
 template <typename R, bool ADJ>
 __global__ void __launch_bounds__(kThreads)
 k_rotate_pairs(int64_t npairs, int64_t nlo, const uint32_t *__restrict__ tab, int64_t nhi, int n_lo, int64_t off,
                int64_t dlo, int64_t m, uint64_t x, const uint64_t *__restrict__ z, const double2 *__restrict__ c,
-               R theta, typename Cx<R>::T *phi, typename Cx<R>::T *lam, double *partials) {
+               R theta, RotAngles<R> ra, typename Cx<R>::T *phi, typename Cx<R>::T *lam, double *partials) {
     using C2 = typename Cx<R>::T;
     __shared__ uint64_t sm_z[kRotPairTerms];
     __shared__ C2 sm_c[kRotPairTerms];
@@ -276,19 +289,33 @@ k_rotate_pairs(int64_t npairs, int64_t nlo, const uint32_t *__restrict__ tab, in
         const int64_t h = i / nlo, l = i - h * nlo;
         const uint64_t t = ((uint64_t)__ldg(pat_hi + h) << n_lo) | (uint64_t)__ldg(pat_lo + l);
         const uint64_t s = t ^ x;
-        R fr = R(0), fi = R(0);
-        for (int k = 0; k < m; ++k) {
-            const uint32_t par = __popcll(sm_z[k] & s);
-            fr += flip(sm_c[k].x, par);
-            fi += flip(sm_c[k].y, par);
+        R fr = R(0), fi = R(0), cs, q;
+        if (ra.np != 0) {
+            const uint64_t tm = t & ra.S;
+            int kk = -1;
+#pragma unroll
+            for (int k = 0; k < kActMax; ++k)
+                if (k < ra.np && tm == ra.pat[k]) kk = k;
+            if (kk < 0) continue;  // f = 0: the pair does not rotate
+            const uint32_t par = __popcll(ra.zo & s);
+            fr = flip(ra.fr[kk], par);
+            fi = flip(ra.fi[kk], par);
+            cs = ra.cs[kk];
+            q = ra.q[kk];
+        } else {
+            for (int k = 0; k < m; ++k) {
+                const uint32_t par = __popcll(sm_z[k] & s);
+                fr += flip(sm_c[k].x, par);
+                fi += flip(sm_c[k].y, par);
+            }
+            const R mag = sqrt(fr * fr + fi * fi);
+            if (mag == R(0)) continue;
+            R sn;
+            sincos_r<R>(theta * mag, &sn, &cs);
+            q = sn / mag;
         }
-        const R mag = sqrt(fr * fr + fi * fi);
-        if (mag == R(0)) continue;
         const int64_t it = off + (int64_t)__ldg(rt_hi + h) * dlo + __ldg(rt_lo + l);
         const int64_t is = off + (int64_t)__ldg(rs_hi + h) * dlo + __ldg(rs_lo + l);
-        R sn, cs;
-        sincos_r<R>(theta * mag, &sn, &cs);
-        const R q = sn / mag;
         auto rot = [&](const C2 &u, const C2 &w, C2 &nu, C2 &nw) {
             const R wr = fr * w.x - fi * w.y, wi = fr * w.y + fi * w.x;
             const R ur = fr * u.x + fi * u.y, ui = fr * u.y - fi * u.x;
@@ -626,6 +653,14 @@ const RotPairs *rotation_pairs(pauli_sum *G, const pauli_sector *sec, uint64_t x
     rp.sector_uid = sec->uid;
     rp.leaks = rotation_leaks(G, v, x, st) ? 1 : 0;
     if (!rp.leaks) {
+        {
+            std::vector<uint64_t> hz(G->m);
+            std::vector<double2> hc(G->m);
+            PS_CUDA(cudaMemcpyAsync(hz.data(), G->z, G->m * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+            PS_CUDA(cudaMemcpyAsync(hc.data(), G->c, G->m * sizeof(double2), cudaMemcpyDeviceToHost, st));
+            PS_CUDA(cudaStreamSynchronize(st));
+            rp.act = find_active_patterns(x, hz.data(), hc.data(), G->m);
+        }
         const uint32_t lomask = (uint32_t)((1ull << v.n_lo) - 1ull);
         const uint32_t xlo = (uint32_t)(x & lomask), xhi = (uint32_t)(x >> v.n_lo);
         const int b0 = __builtin_ctzll(x);
@@ -657,8 +692,21 @@ template <typename R, bool ADJ>
 static void launch_pairs(const RotPairs &rp, pauli_sum *G, const SectorView &v, uint64_t x, double theta, void *phi,
                          void *lam, double *partials, unsigned grid, cudaStream_t st) {
     using C2 = typename Cx<R>::T;
+    RotAngles<R> ra;
+    const ActivePatterns &ap = rp.act;
+    ra.S = ap.S;
+    ra.zo = ap.zo;
+    ra.np = ap.np;
+    for (int k = 0; k < kActMax; ++k) {
+        const double mag = std::hypot(ap.F[k].x, ap.F[k].y);
+        ra.pat[k] = ap.pat[k];
+        ra.fr[k] = (R)ap.F[k].x;
+        ra.fi[k] = (R)ap.F[k].y;
+        ra.cs[k] = (R)std::cos(theta * mag);
+        ra.q[k] = (R)(mag > 0.0 ? std::sin(theta * mag) / mag : 0.0);
+    }
     k_rotate_pairs<R, ADJ><<<grid, kThreads, 0, st>>>(rp.nlo * rp.nhi, rp.nlo > 0 ? rp.nlo : 1, rp.tab, rp.nhi,
-                                                     v.n_lo, v.off[0], v.dlo[0], G->m, x, G->z, G->c, (R)theta,
+                                                     v.n_lo, v.off[0], v.dlo[0], G->m, x, G->z, G->c, (R)theta, ra,
                                                      static_cast<C2 *>(phi), static_cast<C2 *>(lam), partials);
     PS_LAUNCH_CHECK();
 }

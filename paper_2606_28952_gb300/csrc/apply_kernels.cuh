@@ -683,12 +683,14 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
     }
 }
 
-// Four or more FP32 columns a thread: a register budget of four resident CTAs
-// (64 registers a thread), which the compiler picks by itself for a real
-// operator and otherwise undershoots with spills; every other instantiation
-// keeps the compiler's own allocation.
+// Register budgets: four or more FP32 columns a thread take the budget of
+// four resident CTAs (64 registers a thread) where the compiler's own choice
+// spills (a complex operator, or two staged rows); the real operator with one
+// staged row (64 registers by itself, and measurably faster without the
+// bound) and every other instantiation keep the compiler's own allocation
+// (a minimum of 0 CTAs per SM states no bound).
 template <typename R, int KIND, bool REALH, int TPT, int NBUF>
-__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && TPT >= 4) ? 4 : 1)
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 && TPT >= 4 && !(REALH && NBUF == 1)) ? 4 : 0)
 k_apply(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__restrict__ psi,
         typename Cx<R>::T *__restrict__ out, double *__restrict__ partials, int flags) {
     extern __shared__ __align__(16) char smem[];

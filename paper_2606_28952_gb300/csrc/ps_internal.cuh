@@ -247,11 +247,29 @@ constexpr int kLocMaxGroups = 512;
 // members in the block, each listed once (the member with the lowest bit of x
 // set): pair i = h * nlo + l has t = (pat_hi[h] << n_lo) | pat_lo[l], index of t
 // off + rt_hi[h] * D_lo + rt_lo[l] and index of t ^ x off + rs_hi[h] * D_lo + rs_lo[l].
+// Active pair patterns of a single-X-mask sum G = sum_k C_k X^x Z^{z_k}.
+// With D = OR_k (z_k ^ z_0), S = x | D and z_o = z_0 & ~S,
+//   f(s) = sum_k C_k (-1)^{z_k . s} = (-1)^{z_o . s} F(s & S),
+// so whether a pair {t, t ^ x} rotates, and by how much, depends only on the
+// pattern q = t & S.  np > 0: the np patterns q (bit b0 of x set; any q when
+// x = 0) with F(q ^ x) != 0 and those F values, summed in the order of the
+// terms; np = -1: no pattern is active; np = 0: not tabulated (S wider than
+// 14 bits or more than kActMax active patterns).
+constexpr int kActMax = 4;
+struct ActivePatterns {
+    uint64_t S = 0, zo = 0;
+    uint64_t pat[kActMax] = {};
+    double2 F[kActMax] = {};
+    int np = 0;
+};
+ActivePatterns find_active_patterns(uint64_t x, const uint64_t *z, const double2 *c, int64_t m);  // rotseq.cu
+
 struct RotPairs {
     uint64_t sector_uid = 0;
     int leaks = -1;            // the generator moves amplitude out of the sector: -1 unknown
     int64_t nlo = 0, nhi = 0;  // table entries per half
     uint32_t *tab = nullptr;   // pat_lo, rt_lo, rs_lo [nlo] each, then pat_hi, rt_hi, rs_hi [nhi]
+    ActivePatterns act;        // the generator's active patterns (np > 0: angles per pattern on the host)
 };
 constexpr int kRotPairsCache = 4;
 constexpr int kRotPairTerms = 512;  // generators with more terms keep the per-target kernel
@@ -286,6 +304,8 @@ struct pauli_sum {
     int *leak_flag = nullptr;             // device word of the one-time leak check
     ps::Plan plans[4];
     int nplans = 0;
+    double *rows_part = nullptr;          // [rows_cap][4] partials of pauli_expect_rows
+    int64_t rows_cap = 0;
 };
 
 struct pauli_sector {
@@ -299,6 +319,10 @@ struct pauli_sector {
 namespace ps {
 constexpr uint32_t kSumMagic = 0x50534d31u;     // "PSM1"
 constexpr uint32_t kSectorMagic = 0x50534331u;  // "PSC1"
+
+// rows.cu: selected rows of H psi (one CTA per target index)
+void launch_apply_rows(const pauli_sum *H, const SectorView &v, const void *psi, const int64_t *rows, int64_t nrows,
+                       void *out, int dtype, double *partials, cudaStream_t st);
 
 // build.cu
 void to_xz_device(int64_t m, const uint64_t *x, const uint64_t *z, const uint8_t *gamma,

@@ -37,7 +37,10 @@ namespace {
 enum : int { RS_ROW = 0, RS_COL = 1, RS_PAIR = 2, RS_EACH = 3 };
 constexpr int kSeqThreads = 512;
 
-constexpr int kMaxActive = 4;   // active pair patterns kept per generator
+constexpr int kMaxActive = kActMax;   // active pair patterns kept per generator
+constexpr int kGenChunk = 32;         // generator records staged in shared memory at a time
+// dynamic shared memory of a tile: 227 KB less the staged records and angles
+constexpr size_t kSeqDynMax = 218 * 1024;
 
 struct SeqGen {
     uint64_t x;
@@ -52,6 +55,7 @@ struct SeqGen {
     int pad;
     int *status;   // the generator's device status word (sector leaks)
 };
+static_assert(sizeof(SeqGen) % 8 == 0, "records are staged as 8-byte words");
 
 struct SeqArgs {
     const SeqGen *gens;
@@ -95,7 +99,7 @@ __device__ __forceinline__ void seq_entry(int e, int ld, int lw, int &rs, int &c
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(kSeqThreads)
+__global__ void __launch_bounds__(kSeqThreads, 2)
 k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
     using C2 = typename Cx<R>::T;
     extern __shared__ __align__(16) char smem[];
@@ -147,84 +151,127 @@ k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
         tile[e] = psi[off + rowrank * dlo + c0 + cc];
     }
     __syncthreads();
-    // 2. the run's rotations, in order; a target is skipped unless its pair can
-    //    rotate (its pattern on the generator's support is active)
-    for (int gi = A.g0; gi < A.g1; ++gi) {
-        const SeqGen &g = A.gens[gi];
-        const uint64_t gx = g.x, gm = g.m;
-        const int np = g.np, b0 = g.b0;
-        uint64_t pat[kMaxActive];
-#pragma unroll
-        for (int k = 0; k < kMaxActive; ++k) pat[k] = g.pat[k];
-        const R theta = (R)__ldg(A.theta + g.theta);
-        for (int e = tid; e < nent; e += kSeqThreads) {
-            int rs, cc;
-            seq_entry<MODE>(e, ld, A.lw, rs, cc);
-            if (cc >= ncol) continue;
-            const uint32_t thi = thi_s[rs], tlo = tlo_s[cc];
-            const uint64_t t = (uint64_t)tlo | ((uint64_t)thi << v.n_lo);
-            const uint64_t s = t ^ gx;   // the pair partner (t itself for a diagonal generator)
-            R fr = R(0), fi = R(0);
-            if (np != 0) {
-                const uint64_t tm = t & gm;
-                int kk = -1;
-#pragma unroll
-                for (int k = 0; k < kMaxActive; ++k)
-                    if (k < np && tm == pat[k]) kk = k;
-                if (kk < 0) continue;
-                const double2 F = g.F[kk];
-                const uint32_t par = __popcll(g.zo & s);
-                fr = flip((R)F.x, par);
-                fi = flip((R)F.y, par);
-            } else {
-                if (gx != 0 && !((t >> b0) & 1ull)) continue;  // each pair from its member with bit b0 set
-                phase_sum<R>(A, g, s, fr, fi);
-            }
-            if (gx == 0) {
-                // exp(-i theta f_t) on one amplitude (f real for a Hermitian diagonal generator)
-                R sn, cs;
-                sincos_s<R>(theta * fr, &sn, &cs);
-                const C2 a = tile[e];
-                C2 o;
-                o.x = cs * a.x + sn * a.y;
-                o.y = cs * a.y - sn * a.x;
-                tile[e] = o;
-                continue;
-            }
-            const uint32_t slo = (uint32_t)(s & lomask), shi = (uint32_t)(s >> v.n_lo);
-            bool in = cls_lo(v, slo) == klo && cls_hi(v, shi) == khi;
-            int pe = 0;
-            if (in) {
-                if (MODE == RS_COL) {
-                    pe = ((int)__ldg(v.rank_hi + shi) << A.lw) + cc;
-                } else {
-                    int prs = rs;
-                    if (shi != thi) prs = (nrow == 2 && shi == rpat[rs ^ 1]) ? (rs ^ 1) : -1;
-                    if (prs < 0) in = false;
-                    else pe = prs * ld + (int)__ldg(v.rank_lo + slo);
-                }
-            }
-            if (!in) {
-                if (fr != R(0) || fi != R(0)) atomicCAS(g.status, 0, (int)PAULI_ESECTOR);
-                continue;
-            }
-            const R mag = sqrt(fr * fr + fi * fi);
-            if (mag == R(0)) continue;
-            R sn, cs;
-            sincos_s<R>(theta * mag, &sn, &cs);
-            const R q = sn / mag;
-            const C2 a = tile[e], b = tile[pe];
-            const R wr = fr * b.x - fi * b.y, wi = fr * b.y + fi * b.x;   // f b
-            const R ur = fr * a.x + fi * a.y, ui = fr * a.y - fi * a.x;   // conj(f) a
-            C2 na, nb;
-            na.x = cs * a.x + q * wi;
-            na.y = cs * a.y - q * wr;
-            nb.x = cs * b.x + q * ui;
-            nb.y = cs * b.y - q * ur;
-            tile[e] = na;
-            tile[pe] = nb;
+    // 2. the run's rotations, in order, kGenChunk generator records at a time
+    //    staged in shared memory with their angles and, per active pattern,
+    //    cos / sin of the pattern's angle; a target is skipped unless its pair
+    //    can rotate (its pattern on the generator's support is active)
+    __shared__ SeqGen sg[kGenChunk];
+    __shared__ R s_th[kGenChunk];
+    __shared__ R s_cs[kGenChunk][kMaxActive], s_q[kGenChunk][kMaxActive];
+    for (int c0g = A.g0; c0g < A.g1; c0g += kGenChunk) {
+        const int nc = min(kGenChunk, A.g1 - c0g);
+        {
+            const uint64_t *src = reinterpret_cast<const uint64_t *>(A.gens + c0g);
+            uint64_t *dst = reinterpret_cast<uint64_t *>(sg);
+            for (int wd = tid; wd < nc * (int)(sizeof(SeqGen) / 8); wd += kSeqThreads) dst[wd] = __ldg(src + wd);
         }
         __syncthreads();
+        if (tid < nc * kMaxActive) {
+            const int gi = tid / kMaxActive, k = tid - gi * kMaxActive;
+            const SeqGen &g = sg[gi];
+            const double th = __ldg(A.theta + g.theta);
+            if (k == 0) s_th[gi] = (R)th;
+            double cs = 1.0, q = 0.0;
+            if (k < g.np) {
+                const double2 F = g.F[k];
+                if (g.x == 0) {
+                    // diagonal: exp(-i theta f) with f = +-F (real); the sign goes on the sine
+                    cs = cos(th * F.x);
+                    q = sin(th * F.x);
+                } else {
+                    const double mag = hypot(F.x, F.y);
+                    cs = cos(th * mag);
+                    q = sin(th * mag) / mag;
+                }
+            }
+            s_cs[gi][k] = (R)cs;
+            s_q[gi][k] = (R)q;
+        }
+        __syncthreads();
+        for (int gi = 0; gi < nc; ++gi) {
+            const SeqGen &g = sg[gi];
+            const uint64_t gx = g.x, gm = g.m, gzo = g.zo;
+            const int np = g.np, b0 = g.b0;
+            const R theta = s_th[gi];
+            for (int e = tid; e < nent; e += kSeqThreads) {
+                int rs, cc;
+                seq_entry<MODE>(e, ld, A.lw, rs, cc);
+                if (cc >= ncol) continue;
+                const uint32_t thi = thi_s[rs], tlo = tlo_s[cc];
+                const uint64_t t = (uint64_t)tlo | ((uint64_t)thi << v.n_lo);
+                const uint64_t s = t ^ gx;   // the pair partner (t itself for a diagonal generator)
+                R fr = R(0), fi = R(0), cs, q;
+                if (np != 0) {
+                    const uint64_t tm = t & gm;
+                    int kk = -1;
+#pragma unroll
+                    for (int k = 0; k < kMaxActive; ++k)
+                        if (k < np && tm == g.pat[k]) kk = k;
+                    if (kk < 0) continue;
+                    const uint32_t par = __popcll(gzo & s);
+                    const double2 F = g.F[kk];
+                    fr = flip((R)F.x, par);
+                    fi = flip((R)F.y, par);
+                    cs = s_cs[gi][kk];
+                    q = (gx == 0) ? flip(s_q[gi][kk], par) : s_q[gi][kk];
+                } else {
+                    if (gx != 0 && !((t >> b0) & 1ull)) continue;  // each pair from its member with bit b0 set
+                    phase_sum<R>(A, g, s, fr, fi);
+                    if (gx == 0) {
+                        sincos_s<R>(theta * fr, &q, &cs);
+                    } else {
+                        const R mag = sqrt(fr * fr + fi * fi);
+                        if (mag == R(0)) {
+                            cs = R(1);
+                            q = R(0);
+                        } else {
+                            R sn;
+                            sincos_s<R>(theta * mag, &sn, &cs);
+                            q = sn / mag;
+                        }
+                    }
+                }
+                if (gx == 0) {
+                    // exp(-i theta f_t) on one amplitude (f real for a Hermitian diagonal
+                    // generator): cs = cos(theta f_t), q = sin(theta f_t)
+                    const C2 a = tile[e];
+                    C2 o;
+                    o.x = cs * a.x + q * a.y;
+                    o.y = cs * a.y - q * a.x;
+                    tile[e] = o;
+                    continue;
+                }
+                const uint32_t slo = (uint32_t)(s & lomask), shi = (uint32_t)(s >> v.n_lo);
+                bool in = cls_lo(v, slo) == klo && cls_hi(v, shi) == khi;
+                int pe = 0;
+                if (in) {
+                    if (MODE == RS_COL) {
+                        pe = ((int)__ldg(v.rank_hi + shi) << A.lw) + cc;
+                    } else {
+                        int prs = rs;
+                        if (shi != thi) prs = (nrow == 2 && shi == rpat[rs ^ 1]) ? (rs ^ 1) : -1;
+                        if (prs < 0) in = false;
+                        else pe = prs * ld + (int)__ldg(v.rank_lo + slo);
+                    }
+                }
+                if (!in) {
+                    if (fr != R(0) || fi != R(0)) atomicCAS(g.status, 0, (int)PAULI_ESECTOR);
+                    continue;
+                }
+                if (q == R(0) && cs == R(1)) continue;  // f = 0 (or a zero angle): nothing moves
+                const C2 a = tile[e], b = tile[pe];
+                const R wr = fr * b.x - fi * b.y, wi = fr * b.y + fi * b.x;   // f b
+                const R ur = fr * a.x + fi * a.y, ui = fr * a.y - fi * a.x;   // conj(f) a
+                C2 na, nb;
+                na.x = cs * a.x + q * wi;
+                na.y = cs * a.y - q * wr;
+                nb.x = cs * b.x + q * ui;
+                nb.y = cs * b.y - q * ur;
+                tile[e] = na;
+                tile[pe] = nb;
+            }
+            __syncthreads();
+        }
     }
     // 3. the tile -> psi
     for (int e = tid; e < nent; e += kSeqThreads) {
@@ -286,59 +333,62 @@ int col_lw(const SectorView &v, size_t es) {
     int lw = es == 8 ? 2 : 1;
     const int64_t want = 2 * (int64_t)num_sms();
     while (lw > 0 && ((v.dlo[0] + (1ll << lw) - 1) >> lw) < want) --lw;
-    while (lw > 0 && tile_bytes(v.dhi[0], 1ll << lw, es) > 226 * 1024) --lw;
+    while (lw > 0 && tile_bytes(v.dhi[0], 1ll << lw, es) > kSeqDynMax) --lw;
     return lw;
 }
 
-// Active pairs of one generator.  With D = OR_k (z_k ^ z_0), S = x | D and
-// z_o = z_0 & ~S, f(s) = sum_k c_k (-1)^{z_k . s} = (-1)^{z_o . s} F(s & S),
-// F(r) = sum_k c_k (-1)^{z_k . r} (every term has the same Z bits outside S).
-// Whether a pair {t, t ^ x} rotates, and by how much, depends only on the
-// target's pattern q = t & S; every q that represents a pair (bit b0 of x set;
-// every q when x is 0) with F(q ^ x) != 0 is kept, with F(q ^ x) summed in the
-// order of the terms (the order of the per-target sum, so the complex128 values
-// are the same bits), when S has at most 14 bits and at most kMaxActive
-// patterns are active (np = -1: none is; np = 0: the test is off and every
-// representative sums its terms).
-void active_patterns(SeqGen &g, const std::vector<uint64_t> &hz, const std::vector<double2> &hc) {
-    g.np = 0;
-    g.m = 0;
-    g.zo = 0;
-    for (int k = 0; k < kMaxActive; ++k) {
-        g.pat[k] = 0;
-        g.F[k] = make_double2(0.0, 0.0);
-    }
-    if (hz.empty()) return;
+}  // namespace
+
+ActivePatterns ps::find_active_patterns(uint64_t x, const uint64_t *z, const double2 *c, int64_t m) {
+    ActivePatterns ap;
+    if (m <= 0) return ap;
     uint64_t d = 0;
-    for (uint64_t z : hz) d |= z ^ hz[0];
-    const uint64_t S = g.x | d;
-    if (__builtin_popcountll(S) > 14) return;
+    for (int64_t k = 0; k < m; ++k) d |= z[k] ^ z[0];
+    const uint64_t S = x | d;
+    if (__builtin_popcountll(S) > 14) return ap;
+    const int b0 = x ? __builtin_ctzll(x) : -1;
     std::vector<uint64_t> act;
     std::vector<double2> fval;
     uint64_t q = 0;
     do {
-        if (g.x == 0 || ((q >> g.b0) & 1ull)) {
-            const uint64_t sq = q ^ g.x;
+        if (x == 0 || ((q >> b0) & 1ull)) {
+            const uint64_t sq = q ^ x;  // the partner's bits on S (x lies inside S)
             double fr = 0.0, fi = 0.0;
-            for (size_t t = 0; t < hz.size(); ++t) {
-                const bool odd = __builtin_popcountll(hz[t] & sq) & 1;
-                fr += odd ? -hc[t].x : hc[t].x;
-                fi += odd ? -hc[t].y : hc[t].y;
+            for (int64_t k = 0; k < m; ++k) {
+                const bool odd = __builtin_popcountll(z[k] & sq) & 1;
+                fr += odd ? -c[k].x : c[k].x;
+                fi += odd ? -c[k].y : c[k].y;
             }
             if (fr != 0.0 || fi != 0.0) {
                 act.push_back(q);
                 fval.push_back(make_double2(fr, fi));
-                if ((int)act.size() > kMaxActive) return;
+                if ((int)act.size() > kActMax) return ap;
             }
         }
         q = (q - S) & S;  // next subset of S
     } while (q != 0);
-    g.m = S;
-    g.zo = hz[0] & ~S;
-    g.np = act.empty() ? -1 : (int)act.size();
+    ap.S = S;
+    ap.zo = z[0] & ~S;
+    ap.np = act.empty() ? -1 : (int)act.size();
     for (size_t k = 0; k < act.size(); ++k) {
-        g.pat[k] = act[k];
-        g.F[k] = fval[k];
+        ap.pat[k] = act[k];
+        ap.F[k] = fval[k];
+    }
+    return ap;
+}
+
+namespace {
+
+// The rotation-sequence record's copy of the generator's active patterns
+// (the per-target sums in term order: the complex128 values are the same bits).
+void active_patterns(SeqGen &g, const std::vector<uint64_t> &hz, const std::vector<double2> &hc) {
+    const ActivePatterns ap = find_active_patterns(g.x, hz.data(), hc.data(), (int64_t)hz.size());
+    g.np = ap.np;
+    g.m = ap.S;
+    g.zo = ap.zo;
+    for (int k = 0; k < kMaxActive; ++k) {
+        g.pat[k] = ap.pat[k];
+        g.F[k] = ap.F[k];
     }
 }
 
@@ -513,7 +563,7 @@ int pauli_rotseq_info(const pauli_rotseq *q, int dtype, int *launches, int *fuse
         const size_t es = dtype == PAULI_C64 ? 8 : 16;
         int nl = 0, nf = 0;
         for (const auto &r : q->runs) {
-            if (r.mode != RS_EACH && run_smem(r, q->s->v, es) <= 226 * 1024) {
+            if (r.mode != RS_EACH && run_smem(r, q->s->v, es) <= kSeqDynMax) {
                 ++nl;
                 nf += r.g1 - r.g0;
             } else {
@@ -544,7 +594,7 @@ int pauli_rotseq_apply(pauli_rotseq *q, const double *thetas, void *psi, int dty
         PS_CUDA(cudaMemcpyAsync(q->d_theta, thetas, (size_t)q->K * sizeof(double), cudaMemcpyHostToDevice, cs));
         const size_t es = dtype == PAULI_C64 ? 8 : 16;
         for (const auto &run : q->runs) {
-            if (run.mode != RS_EACH && run_smem(run, q->s->v, es) <= 226 * 1024) {
+            if (run.mode != RS_EACH && run_smem(run, q->s->v, es) <= kSeqDynMax) {
                 if (dtype == PAULI_C64) launch_run<float>(q, run, psi, cs);
                 else launch_run<double>(q, run, psi, cs);
                 continue;

@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import MLP, PauliSum, Pool, Sector, expect, rotate_adjoint, rotate_seq
+from . import MLP, PauliSum, Pool, Sector, expect, expect_rows, rotate_adjoint, rotate_seq
 
 
 # ---------------------------------------------------------------------------
@@ -60,9 +60,16 @@ class EnergyGradient:
     One evaluation: copy |ref>, K rotations, one pauli_expect that also keeps
     lam = H psi, then K fused adjoint launches (k = K-1 .. 0) that each add
     <lam|G_k|phi> to a device array and undo U_k on phi and lam; a single
-    device-to-host copy brings E and the K gradient entries back."""
+    device-to-host copy brings E and the K gradient entries back.
 
-    def __init__(self, H: PauliSum, sector: Sector, ansatz: ProductAnsatz, dtype=None, device="cuda"):
+    ``rows`` (sector indices, device int64): a set of configurations that every
+    generator maps onto itself and that holds the reference, so psi(theta)
+    vanishes off it.  Then pauli_expect_rows gives E and lam = P H psi (P the
+    projector on the rows) from those rows alone; the rotations keep P lam and
+    (1 - P) lam apart, and <lam|G_k|phi> only sees P lam, so the gradient is
+    the same as with the full H psi."""
+
+    def __init__(self, H: PauliSum, sector: Sector, ansatz: ProductAnsatz, dtype=None, device="cuda", rows=None):
         import torch
         self.torch = torch
         self.H, self.s, self.ansatz = H, sector, ansatz
@@ -71,9 +78,19 @@ class EnergyGradient:
         self.ref = torch.zeros(sector.dim, dtype=self.dtype, device=device)
         self.ref[ansatz.ref_index] = 1.0
         self.psi = torch.empty_like(self.ref)
-        self.lam = torch.empty_like(self.ref)
+        self.lam = torch.zeros_like(self.ref) if rows is not None else torch.empty_like(self.ref)
+        self.rows = rows
         self.res = torch.zeros(4 + 2 * K, dtype=torch.float64, device=device)
         self.evals = 0
+
+    def _expect(self, hpsi_out=None):
+        if self.rows is None:
+            expect(self.H, self.s, self.psi, hpsi_out=hpsi_out, result=self.res[:4])
+        else:
+            if hpsi_out is not None:
+                # entries off the rows stay zero: the adjoint sweep rotates zeros into zeros
+                hpsi_out.zero_()
+            expect_rows(self.H, self.s, self.psi, self.rows, hpsi_out=hpsi_out, result=self.res[:4])
 
     def state(self, theta):
         self.psi.copy_(self.ref)
@@ -82,14 +99,14 @@ class EnergyGradient:
 
     def energy(self, theta) -> float:
         self.state(theta)
-        expect(self.H, self.s, self.psi, result=self.res[:4])
+        self._expect()
         self.evals += 1
         return float(self.res[0].item())
 
     def __call__(self, theta):
         theta = np.asarray(theta, dtype=np.float64)
         self.state(theta)
-        expect(self.H, self.s, self.psi, hpsi_out=self.lam, result=self.res[:4])
+        self._expect(hpsi_out=self.lam)
         gens = self.ansatz.generators
         for k in range(len(gens) - 1, -1, -1):
             rotate_adjoint(gens[k], self.s, -float(theta[k]), self.psi, self.lam, self.res[4 + 2 * k:6 + 2 * k])

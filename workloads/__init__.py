@@ -260,6 +260,15 @@ def pair_double_ansatz(norb: int, count: int):
     return out[:count]
 
 
+def seniority_zero_configs(norb: int, npairs: int) -> np.ndarray:
+    """Every configuration whose beta string equals its alpha string (alpha in
+    the low norb bits, beta in the high ones), npairs electrons of each spin,
+    ascending: the configurations a pair-double ansatz reaches from a
+    closed-shell reference.  C(norb, npairs) entries (uint64)."""
+    out = [a | (a << norb) for a in range(1 << norb) if bin(a).count("1") == npairs]
+    return np.array(sorted(out), dtype=np.uint64)
+
+
 def double_generator(modes_c, modes_a):
     """G = i (T - T^dagger), T = a+_{c0} a+_{c1} a_{a1} a_{a0} (creation modes c,
     annihilation modes a, spin-orbital indices)."""
