@@ -104,13 +104,17 @@ int g_sms[kMaxDev] = {};
 }  // namespace
 
 void smem_optin(const void *func, size_t bytes) {
-    if (bytes <= 48 * 1024) return;
+    // without the opt-in a block gets 48 KB of shared memory, static and dynamic together
+    if (bytes == 0) return;
     int dev = 0;
     PS_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_attr_mu);
     size_t &have = g_attr[std::make_pair(dev, func)];
     if (have >= bytes) return;
-    PS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cudaFuncAttributes fa;
+    PS_CUDA(cudaFuncGetAttributes(&fa, func));
+    if (bytes + fa.sharedSizeBytes > 48 * 1024)
+        PS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     have = bytes;
 }
 

@@ -52,6 +52,7 @@ struct SeqGen {
     int theta;     // index into the angle array
     int b0;        // lowest set bit of x (-1 for x = 0)
     int np;        // number of active patterns; 0: every pair representative is evaluated
+    int l0, l1;    // the generator's entries in the pair lists (list kernels)
     int pad;
     int *status;   // the generator's device status word (sector leaks)
 };
@@ -283,6 +284,234 @@ k_rotseq(SectorView v, SeqArgs A, typename Cx<R>::T *__restrict__ psi) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// List kernels.  When every generator of a run has tabulated active patterns
+// and keeps the sector, the pairs it rotates are known before the run: a
+// ROW or PAIR generator rotates column c with column pc of the same (ROW) or
+// the paired (PAIR) row when the row's pattern on S also matches; a COL
+// generator rotates row r with row pr of every column whose pattern matches.
+// Each generator has a list of entries {index, partner | kk << 24 | sgn << 31}
+// (kk: the active pattern, sgn: the parity of z_o on the partner's listed
+// half), so a tile visits only the targets that rotate instead of testing
+// every amplitude against every generator.
+// ---------------------------------------------------------------------------
+constexpr int kListThreads = 256;
+
+struct ListArgs {
+    const SeqGen *gens;
+    int g0, g1;
+    const double *theta;   // [K] angles (device)
+    const uint2 *lst;      // every generator's entries
+    const int2 *pairs;     // PAIR: the run's row pairs (ranks; y = -1: a row without a partner)
+    int64_t nunits;        // ROW: rows, COL: columns, PAIR: row pairs
+    int per_tile;          // ROW: rows, PAIR: row pairs, COL: 1 << lw columns per tile
+    int lw;                // COL: log2 of the columns per tile
+};
+
+// it -> (it / L, it % L) for it < 2^24: float quotient, corrected by one step
+__device__ __forceinline__ void div_small(int it, int L, float invL, int &qt, int &rm) {
+    qt = __float2int_rz((float)it * invL);
+    if (qt * L > it) --qt;
+    else if ((qt + 1) * L <= it) ++qt;
+    rm = it - qt * L;
+}
+
+template <typename R>
+__device__ __forceinline__ void rotate_pair(typename Cx<R>::T *tile, int ea, int eb, bool diag, R fr, R fi, R cs, R q) {
+    using C2 = typename Cx<R>::T;
+    if (diag) {
+        // exp(-i theta f) on one amplitude: cs = cos(theta f), q = sin(theta f)
+        const C2 a = tile[ea];
+        C2 o;
+        o.x = cs * a.x + q * a.y;
+        o.y = cs * a.y - q * a.x;
+        tile[ea] = o;
+        return;
+    }
+    const C2 a = tile[ea], b = tile[eb];
+    const R wr = fr * b.x - fi * b.y, wi = fr * b.y + fi * b.x;   // f b
+    const R ur = fr * a.x + fi * a.y, ui = fr * a.y - fi * a.x;   // conj(f) a
+    C2 na, nb;
+    na.x = cs * a.x + q * wi;
+    na.y = cs * a.y - q * wr;
+    nb.x = cs * b.x + q * ui;
+    nb.y = cs * b.y - q * ur;
+    tile[ea] = na;
+    tile[eb] = nb;
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kListThreads)
+k_rotseq_list(SectorView v, ListArgs A, typename Cx<R>::T *__restrict__ psi) {
+    using C2 = typename Cx<R>::T;
+    extern __shared__ __align__(16) char smem[];
+    const int tid = threadIdx.x;
+    const int64_t dlo = v.dlo[0], dhi = v.dhi[0], off = v.off[0];
+    const uint32_t *lst_lo = v.list_lo + v.lst_lo_off[0];
+    const uint32_t *lst_hi = v.list_hi + v.lst_hi_off[0];
+    const int n_lo = v.n_lo;
+    const int64_t u0 = (int64_t)blockIdx.x * A.per_tile;
+    int nrow, ncol, ld, nslot = 0;
+    int64_t c0 = 0;
+    if (MODE == RS_ROW) {
+        nrow = (int)min((int64_t)A.per_tile, dhi - u0);
+        ncol = ld = (int)dlo;
+    } else if (MODE == RS_PAIR) {
+        nslot = (int)min((int64_t)A.per_tile, A.nunits - u0);
+        nrow = 2 * nslot;
+        ncol = ld = (int)dlo;
+    } else {
+        ld = 1 << A.lw;
+        c0 = u0;
+        ncol = (int)min((int64_t)ld, dlo - c0);
+        nrow = (int)dhi;
+    }
+    C2 *tile = reinterpret_cast<C2 *>(smem);
+    uint32_t *thi_s = reinterpret_cast<uint32_t *>(smem + (size_t)nrow * ld * sizeof(C2));
+    int *rrank = reinterpret_cast<int *>(thi_s + nrow);
+    uint32_t *tlo_s = reinterpret_cast<uint32_t *>(rrank + nrow);  // COL: [ld]
+    // 1. rows of the tile, then the tile -> shared memory
+    for (int r = tid; r < nrow; r += kListThreads) {
+        int64_t rk;
+        if (MODE == RS_ROW) rk = u0 + r;
+        else if (MODE == RS_PAIR) {
+            const int2 pr = __ldg(A.pairs + u0 + (r >> 1));
+            rk = (r & 1) ? pr.y : pr.x;
+        } else rk = r;
+        rrank[r] = (int)rk;
+        thi_s[r] = rk >= 0 ? __ldg(lst_hi + rk) : 0u;
+    }
+    if (MODE == RS_COL)
+        for (int c = tid; c < ld; c += kListThreads) tlo_s[c] = c < ncol ? __ldg(lst_lo + c0 + c) : 0u;
+    __syncthreads();
+    const int nent = nrow * ld;
+    for (int e = tid; e < nent; e += kListThreads) {
+        int r, c;
+        if (MODE == RS_COL) {
+            r = e >> A.lw;
+            c = e & (ld - 1);
+        } else {
+            r = e / ld;
+            c = e - r * ld;
+        }
+        if (c >= ncol || rrank[r] < 0) continue;
+        tile[e] = psi[off + (int64_t)rrank[r] * dlo + c0 + c];
+    }
+    // 2. the run's rotations in order, records and angles staged per chunk
+    __shared__ SeqGen sg[kGenChunk];
+    __shared__ R s_cs[kGenChunk][kMaxActive], s_q[kGenChunk][kMaxActive];
+    for (int c0g = A.g0; c0g < A.g1; c0g += kGenChunk) {
+        const int nc = min(kGenChunk, A.g1 - c0g);
+        __syncthreads();
+        {
+            const uint64_t *src = reinterpret_cast<const uint64_t *>(A.gens + c0g);
+            uint64_t *dst = reinterpret_cast<uint64_t *>(sg);
+            for (int wd = tid; wd < nc * (int)(sizeof(SeqGen) / 8); wd += kListThreads) dst[wd] = __ldg(src + wd);
+        }
+        __syncthreads();
+        if (tid < nc * kMaxActive) {
+            const int gi = tid / kMaxActive, k = tid - gi * kMaxActive;
+            const SeqGen &g = sg[gi];
+            const double th = __ldg(A.theta + g.theta);
+            double cs = 1.0, q = 0.0;
+            if (k < g.np) {
+                const double2 F = g.F[k];
+                if (g.x == 0) {
+                    cs = cos(th * F.x);
+                    q = sin(th * F.x);
+                } else {
+                    const double mag = hypot(F.x, F.y);
+                    cs = cos(th * mag);
+                    q = sin(th * mag) / mag;
+                }
+            }
+            s_cs[gi][k] = (R)cs;
+            s_q[gi][k] = (R)q;
+        }
+        __syncthreads();
+        for (int gi = 0; gi < nc; ++gi) {
+            const SeqGen &g = sg[gi];
+            const int L = g.l1 - g.l0;
+            const bool diag = g.x == 0;
+            const uint32_t S_hi = (uint32_t)(g.m >> n_lo), zo_hi = (uint32_t)(g.zo >> n_lo);
+            const uint32_t S_lo = (uint32_t)(g.m & ((1ull << n_lo) - 1ull));
+            const uint32_t zo_lo = (uint32_t)(g.zo & ((1ull << n_lo) - 1ull));
+            const bool pairing = MODE == RS_PAIR && (g.x >> n_lo) != 0;
+            const int units = (MODE == RS_COL) ? ncol : (pairing ? nslot : nrow);
+            const int items = (MODE == RS_COL) ? (L << A.lw) : units * L;
+            const float invL = L > 0 ? 1.0f / (float)L : 0.0f;
+            for (int it = tid; it < items; it += kListThreads) {
+                int u, j;
+                if (MODE == RS_COL) {
+                    j = it >> A.lw;
+                    u = it & (ld - 1);
+                    if (u >= ncol) continue;
+                } else {
+                    div_small(it, L, invL, u, j);
+                }
+                const uint2 en = __ldg(A.lst + g.l0 + j);
+                const int kk = (int)((en.y >> 24) & 3u);
+                uint32_t par = en.y >> 31;
+                const int pidx = (int)(en.y & 0xFFFFFFu);
+                int ea, eb;
+                if (MODE == RS_COL) {
+                    // rows en.x -> pidx of column u; the column's pattern must match
+                    const uint32_t tlo = tlo_s[u];
+                    if ((tlo & S_lo) != (uint32_t)(g.pat[kk] & ((1ull << n_lo) - 1ull))) continue;
+                    par ^= __popc(zo_lo & tlo) & 1u;
+                    ea = ((int)en.x << A.lw) + u;
+                    eb = (pidx << A.lw) + u;
+                } else if (pairing) {
+                    // columns en.x -> pidx across the row pair u; the row holding the target
+                    // is the one whose pattern on S matches
+                    const int ra = 2 * u, rb = 2 * u + 1;
+                    if (rrank[rb] < 0) continue;
+                    const uint32_t ph = (uint32_t)(g.pat[kk] >> n_lo);
+                    int rt, rs;
+                    if ((thi_s[ra] & S_hi) == ph) {
+                        rt = ra;
+                        rs = rb;
+                    } else if ((thi_s[rb] & S_hi) == ph) {
+                        rt = rb;
+                        rs = ra;
+                    } else {
+                        continue;
+                    }
+                    par ^= __popc(zo_hi & thi_s[rs]) & 1u;
+                    ea = rt * ld + (int)en.x;
+                    eb = rs * ld + pidx;
+                } else {
+                    // columns en.x -> pidx inside row u; the row's pattern must match
+                    if (rrank[u] < 0) continue;
+                    const uint32_t thi = thi_s[u];
+                    if ((thi & S_hi) != (uint32_t)(g.pat[kk] >> n_lo)) continue;
+                    par ^= __popc(zo_hi & thi) & 1u;
+                    ea = u * ld + (int)en.x;
+                    eb = u * ld + pidx;
+                }
+                const double2 F = g.F[kk];
+                const R cs = s_cs[gi][kk];
+                const R q = diag ? flip(s_q[gi][kk], par) : s_q[gi][kk];
+                rotate_pair<R>(tile, ea, eb, diag, flip((R)F.x, par), flip((R)F.y, par), cs, q);
+            }
+            __syncthreads();
+        }
+    }
+    // 3. the tile -> psi
+    for (int e = tid; e < nent; e += kListThreads) {
+        int r, c;
+        if (MODE == RS_COL) {
+            r = e >> A.lw;
+            c = e & (ld - 1);
+        } else {
+            r = e / ld;
+            c = e - r * ld;
+        }
+        if (c >= ncol || rrank[r] < 0) continue;
+        psi[off + (int64_t)rrank[r] * dlo + c0 + c] = tile[e];
+    }
+}
+
 }  // namespace
 }  // namespace ps
 
@@ -299,6 +528,9 @@ struct pauli_rotseq {
         int g0, g1;
         uint64_t xh;
         int has_local;
+        int list = 0;        // 1: pair lists built (k_rotseq_list)
+        int64_t nunits = 0;  // list kernels: rows (ROW), columns (COL), row pairs (PAIR)
+        int64_t pairs0 = 0;  // PAIR: first row pair in d_pairs
     };
     std::vector<Run> runs;
     std::vector<int> rec_theta;        // angle index of each generator record (fallback launches)
@@ -306,6 +538,8 @@ struct pauli_rotseq {
     uint64_t *d_tz = nullptr;
     double2 *d_tc = nullptr;
     double *d_theta = nullptr;
+    uint2 *d_list = nullptr;   // pair-list entries of every list run's generators
+    int2 *d_pairs = nullptr;   // row pairs of the PAIR list runs
 };
 
 namespace {
@@ -317,6 +551,8 @@ void free_seq(pauli_rotseq *q) {
     dev_free(q->al, q->d_tz);
     dev_free(q->al, q->d_tc);
     dev_free(q->al, q->d_theta);
+    dev_free(q->al, q->d_list);
+    dev_free(q->al, q->d_pairs);
     q->magic = 0;
     delete q;
 }
@@ -390,6 +626,148 @@ void active_patterns(SeqGen &g, const std::vector<uint64_t> &hz, const std::vect
         g.pat[k] = ap.pat[k];
         g.F[k] = ap.F[k];
     }
+}
+
+// Tile of a list run: rows (ROW), row pairs (PAIR) or 2^lw columns (COL) per
+// CTA, at most ~100 KB so that two CTAs share an SM, and at least two tiles per
+// SM where the sector allows; smem = 0 when one unit does not fit.
+struct ListTile {
+    int per_tile = 1, lw = 0;
+    size_t smem = 0;
+};
+ListTile list_tile(const pauli_rotseq::Run &r, const SectorView &v, size_t es) {
+    ListTile t;
+    const int64_t want = 2 * (int64_t)num_sms();
+    const size_t budget = 100 * 1024;
+    const int64_t dlo = v.dlo[0], dhi = v.dhi[0];
+    if (r.mode == RS_COL) {
+        auto bytes = [&](int lw) { return (size_t)dhi * (((size_t)es << lw) + 8) + ((size_t)4 << lw); };
+        int lw = es == 8 ? 2 : 1;
+        while (lw > 0 && ((dlo + (1ll << lw) - 1) >> lw) < want) --lw;
+        while (lw > 0 && bytes(lw) > budget) --lw;
+        t.lw = lw;
+        t.per_tile = 1 << lw;
+        t.smem = bytes(lw) <= kSeqDynMax ? bytes(lw) : 0;
+        return t;
+    }
+    const size_t unit = (r.mode == RS_PAIR ? 2 : 1) * ((size_t)dlo * es + 8);
+    const int64_t fit = (int64_t)(budget / unit);
+    const int64_t spread = std::max<int64_t>(1, r.nunits / want);
+    t.per_tile = (int)std::max<int64_t>(1, std::min(fit, spread));
+    t.smem = (size_t)t.per_tile * unit <= kSeqDynMax ? (size_t)t.per_tile * unit : 0;
+    return t;
+}
+
+template <typename R>
+void launch_run_list(const pauli_rotseq *q, const pauli_rotseq::Run &r, const ListTile &t, void *psi,
+                     cudaStream_t st) {
+    using C2 = typename Cx<R>::T;
+    const SectorView &v = q->s->v;
+    ListArgs A;
+    A.gens = q->d_gens;
+    A.g0 = r.g0;
+    A.g1 = r.g1;
+    A.theta = q->d_theta;
+    A.lst = q->d_list;
+    A.pairs = q->d_pairs + r.pairs0;
+    A.nunits = r.nunits;
+    A.per_tile = t.per_tile;
+    A.lw = t.lw;
+    const int64_t grid = (r.nunits + t.per_tile - 1) / t.per_tile;
+    if (grid <= 0) return;
+    PS_CHECK(grid < (1ll << 31), PAULI_EUNSUPPORTED, "rotation sequence: too many tiles");
+    C2 *p = static_cast<C2 *>(psi);
+    auto go = [&](auto kern) {
+        smem_optin(reinterpret_cast<const void *>(kern), t.smem);
+        kern<<<(unsigned)grid, kListThreads, t.smem, st>>>(v, A, p);
+        PS_LAUNCH_CHECK();
+    };
+    if (r.mode == RS_ROW) go(k_rotseq_list<R, RS_ROW>);
+    else if (r.mode == RS_PAIR) go(k_rotseq_list<R, RS_PAIR>);
+    else go(k_rotseq_list<R, RS_COL>);
+}
+
+// Pair lists of one run (single product block), or false when a generator is
+// not tabulated or could leave the sector (the run then keeps the scanning kernel).
+struct HostSector {
+    int n_lo, n_hi, klo, khi;
+    std::vector<uint32_t> lstr, hstr, rk_lo, rk_hi;
+};
+bool build_run_lists(const SectorView &v, const HostSector &h, pauli_rotseq::Run &run, std::vector<SeqGen> &gens,
+                     std::vector<uint2> &lst, std::vector<int2> &pairs) {
+    const uint64_t lomask = (1ull << h.n_lo) - 1ull;
+    const int64_t dlo = (int64_t)h.lstr.size(), dhi = (int64_t)h.hstr.size();
+    if (dlo >= (1 << 24) || dhi >= (1 << 24)) return false;
+    for (int gi = run.g0; gi < run.g1; ++gi)
+        if (gens[gi].np == 0) return false;
+    const size_t lst_start = lst.size(), pairs_start = pairs.size();
+    auto fail = [&]() {
+        lst.resize(lst_start);
+        pairs.resize(pairs_start);
+        return false;
+    };
+    for (int gi = run.g0; gi < run.g1; ++gi) {
+        SeqGen &g = gens[gi];
+        g.l0 = (int)lst.size();
+        if (g.np > 0) {
+            const uint32_t xlo = (uint32_t)(g.x & lomask), xhi = (uint32_t)(g.x >> h.n_lo);
+            const uint32_t Slo = (uint32_t)(g.m & lomask), Shi = (uint32_t)(g.m >> h.n_lo);
+            const uint32_t zlo = (uint32_t)(g.zo & lomask), zhi = (uint32_t)(g.zo >> h.n_lo);
+            if (run.mode == RS_COL) {
+                for (int64_t rr = 0; rr < dhi; ++rr) {
+                    const uint32_t thi = h.hstr[rr];
+                    for (int k = 0; k < g.np; ++k) {
+                        if ((thi & Shi) != (uint32_t)(g.pat[k] >> h.n_lo)) continue;
+                        const uint32_t shi = thi ^ xhi;
+                        if (half_cls(shi, v.irr, v.irr_hi) != h.khi) return fail();
+                        const uint32_t sg = (uint32_t)(__builtin_popcount(zhi & shi) & 1);
+                        lst.push_back(make_uint2((uint32_t)rr, h.rk_hi[shi] | ((uint32_t)k << 24) | (sg << 31)));
+                    }
+                }
+            } else {
+                for (int64_t c = 0; c < dlo; ++c) {
+                    const uint32_t tlo = h.lstr[c];
+                    for (int k = 0; k < g.np; ++k) {
+                        if ((tlo & Slo) != (uint32_t)(g.pat[k] & lomask)) continue;
+                        const uint32_t slo = tlo ^ xlo;
+                        if (half_cls(slo, v.irr, v.irr_lo) != h.klo) return fail();
+                        const uint32_t sg = (uint32_t)(__builtin_popcount(zlo & slo) & 1);
+                        lst.push_back(make_uint2((uint32_t)c, h.rk_lo[slo] | ((uint32_t)k << 24) | (sg << 31)));
+                    }
+                }
+                if (xhi != 0) {
+                    // a pairing generator: every row its patterns select needs its partner row
+                    for (int64_t rr = 0; rr < dhi; ++rr)
+                        for (int k = 0; k < g.np; ++k)
+                            if ((h.hstr[rr] & Shi) == (uint32_t)(g.pat[k] >> h.n_lo) &&
+                                half_cls(h.hstr[rr] ^ xhi, v.irr, v.irr_hi) != h.khi)
+                                return fail();
+                }
+            }
+        }
+        g.l1 = (int)lst.size();
+        if (lst.size() >= (size_t)INT_MAX / 2) return fail();
+    }
+    if (run.mode == RS_ROW) {
+        run.nunits = dhi;
+    } else if (run.mode == RS_COL) {
+        run.nunits = dlo;
+    } else {
+        run.pairs0 = (int64_t)pairs.size();
+        const uint32_t xh = (uint32_t)run.xh;
+        for (int64_t i = 0; i < dhi; ++i) {
+            const uint32_t p = h.hstr[i] ^ xh;
+            if (half_cls(p, v.irr, v.irr_hi) == h.khi) {
+                const int64_t j = h.rk_hi[p];
+                if (i < j) pairs.push_back(make_int2((int)i, (int)j));
+            } else if (run.has_local) {
+                pairs.push_back(make_int2((int)i, -1));
+            }
+        }
+        run.nunits = (int64_t)pairs.size() - run.pairs0;
+    }
+    run.list = 1;
+    return true;
 }
 
 size_t run_smem(const pauli_rotseq::Run &r, const SectorView &v, size_t es) {
@@ -483,6 +861,7 @@ int pauli_rotseq_create(pauli_sum *const *Gs, int K, const pauli_sector *s, paul
             g.b0 = x ? __builtin_ctzll(x) : -1;
             g.status = G->status;
             g.pad = 0;
+            g.l0 = g.l1 = 0;
             active_patterns(g, hz, hc);
             gen_of.push_back((int)gens.size());
             gens.push_back(g);
@@ -527,6 +906,26 @@ int pauli_rotseq_create(pauli_sum *const *Gs, int K, const pauli_sector *s, paul
             cur.g1 = r + 1;
         }
         flush();
+        // pair lists for the fused runs (single block with rank tables of at most 2^20 entries)
+        std::vector<uint2> lst;
+        std::vector<int2> pairs;
+        if (single && v.n_lo <= 20 && v.n_hi <= 20) {
+            HostSector h;
+            h.n_lo = v.n_lo;
+            h.n_hi = v.n_hi;
+            h.klo = v.klo[0];
+            h.khi = v.khi[0];
+            h.lstr.resize(v.dlo[0]);
+            h.hstr.resize(v.dhi[0]);
+            h.rk_lo.resize(1ull << v.n_lo);
+            h.rk_hi.resize(1ull << v.n_hi);
+            PS_CUDA(cudaMemcpy(h.lstr.data(), v.list_lo + v.lst_lo_off[0], v.dlo[0] * 4, cudaMemcpyDeviceToHost));
+            PS_CUDA(cudaMemcpy(h.hstr.data(), v.list_hi + v.lst_hi_off[0], v.dhi[0] * 4, cudaMemcpyDeviceToHost));
+            PS_CUDA(cudaMemcpy(h.rk_lo.data(), v.rank_lo, (1ull << v.n_lo) * 4, cudaMemcpyDeviceToHost));
+            PS_CUDA(cudaMemcpy(h.rk_hi.data(), v.rank_hi, (1ull << v.n_hi) * 4, cudaMemcpyDeviceToHost));
+            for (auto &run : q->runs)
+                if (run.mode != RS_EACH) build_run_lists(v, h, run, gens, lst, pairs);
+        }
         for (const SeqGen &g : gens) q->rec_theta.push_back(g.theta);
         // device copies
         q->d_gens = static_cast<SeqGen *>(dev_alloc(q->al, std::max<size_t>(1, gens.size()) * sizeof(SeqGen)));
@@ -538,6 +937,11 @@ int pauli_rotseq_create(pauli_sum *const *Gs, int K, const pauli_sector *s, paul
             PS_CUDA(cudaMemcpy(q->d_tz, tz.data(), tz.size() * 8, cudaMemcpyHostToDevice));
             PS_CUDA(cudaMemcpy(q->d_tc, tc.data(), tc.size() * 16, cudaMemcpyHostToDevice));
         }
+        q->d_list = static_cast<uint2 *>(dev_alloc(q->al, std::max<size_t>(1, lst.size()) * sizeof(uint2)));
+        q->d_pairs = static_cast<int2 *>(dev_alloc(q->al, std::max<size_t>(1, pairs.size()) * sizeof(int2)));
+        if (!lst.empty()) PS_CUDA(cudaMemcpy(q->d_list, lst.data(), lst.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+        if (!pairs.empty())
+            PS_CUDA(cudaMemcpy(q->d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice));
         // the generator of each record, for the fallback launches
         q->G.clear();
         for (int k = 0; k < K; ++k)
@@ -563,7 +967,9 @@ int pauli_rotseq_info(const pauli_rotseq *q, int dtype, int *launches, int *fuse
         const size_t es = dtype == PAULI_C64 ? 8 : 16;
         int nl = 0, nf = 0;
         for (const auto &r : q->runs) {
-            if (r.mode != RS_EACH && run_smem(r, q->s->v, es) <= kSeqDynMax) {
+            const bool fused = r.mode != RS_EACH && ((r.list && list_tile(r, q->s->v, es).smem > 0) ||
+                                                     run_smem(r, q->s->v, es) <= kSeqDynMax);
+            if (fused) {
                 ++nl;
                 nf += r.g1 - r.g0;
             } else {
@@ -594,6 +1000,14 @@ int pauli_rotseq_apply(pauli_rotseq *q, const double *thetas, void *psi, int dty
         PS_CUDA(cudaMemcpyAsync(q->d_theta, thetas, (size_t)q->K * sizeof(double), cudaMemcpyHostToDevice, cs));
         const size_t es = dtype == PAULI_C64 ? 8 : 16;
         for (const auto &run : q->runs) {
+            if (run.mode != RS_EACH && run.list) {
+                const ListTile t = list_tile(run, q->s->v, es);
+                if (t.smem > 0) {
+                    if (dtype == PAULI_C64) launch_run_list<float>(q, run, t, psi, cs);
+                    else launch_run_list<double>(q, run, t, psi, cs);
+                    continue;
+                }
+            }
             if (run.mode != RS_EACH && run_smem(run, q->s->v, es) <= kSeqDynMax) {
                 if (dtype == PAULI_C64) launch_run<float>(q, run, psi, cs);
                 else launch_run<double>(q, run, psi, cs);

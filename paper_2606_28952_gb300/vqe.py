@@ -133,6 +133,8 @@ class LbfgsResult:
 
 def _cubic_min(a, fa, ga, b, fb, gb):
     """Minimiser of the cubic through (a, fa, ga), (b, fb, gb), or None."""
+    if a == b:
+        return None
     d1 = ga + gb - 3.0 * (fa - fb) / (a - b)
     disc = d1 * d1 - ga * gb
     if disc < 0:
@@ -154,6 +156,8 @@ def _zoom(phi, lo, hi, f0, g0, c1, c2, maxit=30):
     for _ in range(maxit):
         a_lo, f_lo, g_lo, _ = lo
         a_hi, f_hi, g_hi, _ = hi
+        if abs(a_hi - a_lo) < 1e-14 * max(1.0, abs(a_lo)):
+            break  # the bracket has collapsed
         a = _cubic_min(a_lo, f_lo, g_lo, a_hi, f_hi, g_hi)
         left, right = min(a_lo, a_hi), max(a_lo, a_hi)
         w = right - left
@@ -187,6 +191,8 @@ def line_search_wolfe(phi, f0, g0, a1=1.0, c1=1e-4, c2=0.9, amax=50.0, maxit=20)
         if ga >= 0:
             return _zoom(phi, (a, fa, ga, data), prev, f0, g0, c1, c2)
         prev = (a, fa, ga, data)
+        if a >= amax:
+            break  # the step cap is reached: take the last step
         a = min(2.0 * a, amax)
     return prev if prev[3] is not None else None
 
