@@ -434,17 +434,26 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
     }
     // full space with a local-pass plan (lattice operators, 2^21 amplitudes or more):
     // chunks staged in shared memory, one pass per local bit set
-    if (v.kind == PAULI_SECTOR_FULL && p.local) {
+    if (v.kind == PAULI_SECTOR_FULL && (p.local || p.local_cl)) {
         const int dflt_local = v.n >= 21 ? 1 : 0;
         if (ch.direct >= 0 ? ch.direct == 2 : dflt_local != 0) {
+            // clustered windows only where installed (ranked = 1) or where the plain
+            // chunks do not fit: they move fewer bytes (two passes instead of three at
+            // 26-30 sites) but the cluster barriers leave the issue-bound gather slower
+            // (30 sites: 35.8 ms against 23.0 ms)
+            bool cl;
+            if (ch.direct == 2 && ch.ranked >= 0) cl = ch.ranked == 1 ? p.local_cl != nullptr : p.local == nullptr;
+            else cl = p.local == nullptr;
             c.local = true;
+            c.local_cl = cl;
+            c.ranked = cl;
             c.direct = false;
             c.smem = 0;
             c.nbuf = 1;
             c.nsplit = 1;
             c.split_p0.assign(2, 0);
             c.split_p0[1] = (int32_t)p.P;
-            c.nct = local_last_chunks(p.local);
+            c.nct = local_last_chunks(cl ? p.local_cl : p.local);
             c.combine_nct = 0;
             return c;
         }
@@ -531,7 +540,7 @@ void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *
     if (cfg.nct == 0) return;
     PS_CHECK(cfg.nct < (1ll << 31), PAULI_EUNSUPPORTED, "apply: too many thread blocks");
     if (cfg.local) {
-        launch_local(p.local, psi_in, psi_out, dtype, v.dim, partials, st);
+        launch_local(cfg.local_cl ? p.local_cl : p.local, psi_in, psi_out, dtype, v.dim, partials, st);
         return;
     }
     PS_CHECK(cfg.smem <= kMaxDynSmem, PAULI_EUNSUPPORTED,

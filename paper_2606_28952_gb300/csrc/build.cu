@@ -499,6 +499,7 @@ void free_plan(const Allocator &al, Plan &p) {
     dev_free(al, p.t_zhi); dev_free(al, p.t_c64); dev_free(al, p.t_c32);
     dev_free(al, p.diag_tab64); dev_free(al, p.diag_tab32); dev_free(al, p.diag_rest);
     free_local_plan(p.local);
+    free_local_plan(p.local_cl);
     free_lists(al, p);
     dev_free(al, p.partials);
     dev_free(al, p.split_buf);

@@ -510,7 +510,8 @@ void free_lists(const Allocator &al, Plan &p) {
 void prepare_for_sector(pauli_sum *H, Plan &p, const SectorView &v, cudaStream_t st) {
     if (v.kind == PAULI_SECTOR_FULL && !p.local_tried) {
         p.local_tried = true;
-        p.local = build_local_plan(H, v.n, st);
+        p.local = build_local_plan(H, v.n, false, st);
+        p.local_cl = build_local_plan(H, v.n, true, st);
     }
     if (v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1 && v.n_lo <= kListMaxLo && v.dlo[0] <= kListMaxDlo &&
         p.I > 0 && !find_lists(p, v.klo[0])) {

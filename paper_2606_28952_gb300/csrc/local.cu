@@ -15,22 +15,30 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "apply_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ps {
 
 namespace {
 
 struct LocalPassDev {
-    int b, m, nn;                  // local bits, high local bits (b - kLocRun), non-local bits
+    int b, m, nn;                  // local bits, high local bits (b - run), non-local bits
+    int run;                       // log2 of the contiguous amplitudes of one staged run
+    int cb;                        // cluster bits (0: one CTA per window)
     int g0, g1;                    // groups of the pass
     int diag;                      // 1: group g0 is the x = 0 group, tabulated
-    int8_t npos[64];               // non-local bit positions, ascending
+    int8_t npos[64];               // non-local bit positions: the cluster bits, then the rest ascending
     const uint64_t *hoff;          // [2^m] global offsets of the high local bits
 };
 
 struct LocalArgs {
     const uint32_t *g_xloc;   // [G'] x compressed to the pass's local bits
+    const uint32_t *g_xcl;    // [G'] x on the cluster bits (the peer CTA's rank offset)
+    const uint64_t *t_xnl;    // [M'] x of the term's group outside the CTA's local bits
     const int32_t *g_t0;      // [G'+1] terms of each group
     const int32_t *g_tz;      // [G'] end of the group's terms with z_loc = 0
     const uint32_t *t_zloc;   // [M'] z compressed to the local bits
@@ -89,22 +97,27 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
         uint64_t k = blockIdx.x;
         for (int i = 0; i < P.nn; ++i, k >>= 1) base |= (k & 1ull) << P.npos[i];
     }
-    // 1. the chunk -> shared memory, 16-byte copies (runs of 2^kLocRun amplitudes)
-    constexpr int kRun = 1 << kLocRun;
+    // this CTA's rank in its cluster: the cluster bits are the lowest of blockIdx.x
+    const uint32_t rank = blockIdx.x & ((1u << P.cb) - 1u);
+    // 1. the chunk -> shared memory, 16-byte copies (runs of 2^run amplitudes)
     constexpr int kPerCopy = 16 / (int)sizeof(C2);  // amplitudes per 16-byte copy
-    constexpr int kCopiesPerRun = kRun / kPerCopy;
+    const int lrun = P.run;
+    const int crun = (1 << lrun) / kPerCopy;        // copies per run (a power of two)
+    const int lcrun = __ffs(crun) - 1;
     const int ncopy = nloc / kPerCopy;
     for (int u = tid; u < ncopy; u += kThreads) {
-        const int run = u / kCopiesPerRun, w = u - run * kCopiesPerRun;
+        const int run = u >> lcrun, w = u & (crun - 1);
         const uint64_t g = base + __ldg(P.hoff + run) + (uint64_t)(w * kPerCopy);
-        cp_async16(chunk + run * kRun + w * kPerCopy, psi + g);
+        cp_async16(chunk + (run << lrun) + w * kPerCopy, psi + g);
     }
     cp_async_commit();
-    // 2. coefficients with the phases of the non-local bits folded in; group records
+    // 2. coefficients with the phases of the non-local bits folded in; group records.
+    //    The source of a term's target differs from it on the group's x, which has
+    //    bits outside the CTA's local set only on the cluster bits (t_xnl).
     for (int t = tid; t < nt; t += kThreads) {
         const int tt = t_first + t;
         const double2 c = __ldg(A.t_c + tt);
-        const bool neg = __popcll(__ldg(A.t_znl + tt) & base) & 1;
+        const bool neg = __popcll(__ldg(A.t_znl + tt) & (base ^ __ldg(A.t_xnl + tt))) & 1;
         C2 cv;
         cv.x = (R)(neg ? -c.x : c.x);
         cv.y = (R)(neg ? -c.y : c.y);
@@ -118,7 +131,7 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
         double ar = 0.0, ai = 0.0;
         for (int tt = A.g_t0[gg]; tt < A.g_tz[gg]; ++tt) {
             const double2 c = __ldg(A.t_c + tt);
-            const bool neg = __popcll(__ldg(A.t_znl + tt) & base) & 1;
+            const bool neg = __popcll(__ldg(A.t_znl + tt) & (base ^ __ldg(A.t_xnl + tt))) & 1;
             ar += neg ? -c.x : c.x;
             ai += neg ? -c.y : c.y;
         }
@@ -126,13 +139,15 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
         a.x = (R)ar;
         a.y = (R)ai;
         sm_a0[g] = a;
-        sm_g[g] = make_int4((int)A.g_xloc[gg], A.g_tz[gg] - t_first, A.g_t0[gg + 1] - t_first, 0);
+        sm_g[g] = make_int4((int)A.g_xloc[gg], A.g_tz[gg] - t_first, A.g_t0[gg + 1] - t_first, (int)A.g_xcl[gg]);
     }
     cp_async_wait<0>();
     __syncthreads();
+    // every chunk of the cluster is staged before any CTA reads a peer's
+    if (P.cb) cg::this_cluster().sync();
     // 3. targets of the chunk, TPT per thread at a time
     ExpAcc<R> ea;
-    constexpr int kLowMask = kRun - 1;
+    const int kLowMask = (1 << lrun) - 1;
     const int g_start = P.diag ? 1 : 0;
     for (int l0 = tid; l0 < nloc; l0 += kThreads * TPT) {
         R accr[TPT], acci[TPT];
@@ -142,7 +157,7 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
             tl[j] = (uint32_t)(l0 + j * kThreads);
-            gidx[j] = base + __ldg(P.hoff + (tl[j] >> kLocRun)) + (tl[j] & kLowMask);
+            gidx[j] = base + __ldg(P.hoff + (tl[j] >> lrun)) + (tl[j] & kLowMask);
             // a later pass adds to the earlier sums: load them now, used after the gather
             if (flags & 8) prev[j] = out[gidx[j]];
         }
@@ -200,9 +215,9 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
             acc2[j].x = accr[j];
             acc2[j].y = acci[j];
         }
-        for (int g = g_start; g < ng; ++g) {
-            const int4 gr = sm_g[g];
-            const C2 a0 = sm_a0[g];
+        // one group's contribution, sources read from `src` (this CTA's chunk, or a
+        // peer's through distributed shared memory when x has cluster bits)
+        auto group = [&](const char *src, const int4 gr, const C2 a0) {
             const uint32_t xb = (uint32_t)gr.x << kEShift;
             if (REALH && gr.z - gr.y == 1) {
                 // one term besides the folded z_loc = 0 ones (a lattice bond: XX + YY)
@@ -212,9 +227,9 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
                 for (int j = 0; j < TPT; ++j) {
                     const uint32_t sb = tb[j] ^ xb;
                     const R f = a0.x + flip(c, __popc(z & sb));
-                    acc_real(acc2[j], f, *reinterpret_cast<const C2 *>(cb + sb));
+                    acc_real(acc2[j], f, *reinterpret_cast<const C2 *>(src + sb));
                 }
-                continue;
+                return;
             }
             R fr[TPT], fi[TPT];
             uint32_t sb[TPT];
@@ -236,13 +251,24 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
             }
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
-                const C2 amp = *reinterpret_cast<const C2 *>(cb + sb[j]);
+                const C2 amp = *reinterpret_cast<const C2 *>(src + sb[j]);
                 if (REALH) {
                     acc_real(acc2[j], fr[j], amp);
                 } else {
                     acc2[j].x += fr[j] * amp.x - fi[j] * amp.y;
                     acc2[j].y += fr[j] * amp.y + fi[j] * amp.x;
                 }
+            }
+        };
+        for (int g = g_start; g < ng; ++g) {
+            const int4 gr = sm_g[g];
+            const C2 a0 = sm_a0[g];
+            if (gr.w == 0) {
+                group(cb, gr, a0);
+            } else {
+                const char *peer = reinterpret_cast<const char *>(
+                    cg::this_cluster().map_shared_rank(chunk, rank ^ (uint32_t)gr.w));
+                group(peer, gr, a0);
             }
         }
 #pragma unroll
@@ -287,6 +313,8 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
             partials[(int64_t)blockIdx.x * 4 + tid] = sum;
         }
     }
+    // no CTA leaves while a peer may still read its chunk
+    if (P.cb) cg::this_cluster().sync();
 }
 
 // T(l) = sum of the x = 0 group's terms with z_nl = 0: c (-1)^popc(z_loc & l)
@@ -318,6 +346,8 @@ uint32_t compress(uint64_t v, const std::vector<int> &pos) {
 
 struct LocalPlan {
     int n = 0, npass = 0;
+    int run = kLocRun;   // log2 of the contiguous amplitudes of a staged run
+    int cb = 0;          // cluster bits: 2^cb CTAs share one window through distributed shared memory
     struct Pass {
         int b = 0, m = 0, nn = 0, g0 = 0, g1 = 0, diag = 0, nt = 0;
         int8_t npos[64] = {};
@@ -326,6 +356,8 @@ struct LocalPlan {
     } pass[kLocMaxPass];
     Allocator al;
     uint32_t *g_xloc = nullptr;
+    uint32_t *g_xcl = nullptr;
+    uint64_t *t_xnl = nullptr;
     int32_t *g_t0 = nullptr, *g_tz = nullptr;
     uint32_t *t_zloc = nullptr;
     uint64_t *t_znl = nullptr;
@@ -342,6 +374,8 @@ void free_local_plan(LocalPlan *lp) {
     if (!lp) return;
     const Allocator &al = lp->al;
     dev_free(al, lp->g_xloc);
+    dev_free(al, lp->g_xcl);
+    dev_free(al, lp->t_xnl);
     dev_free(al, lp->g_t0);
     dev_free(al, lp->g_tz);
     dev_free(al, lp->t_zloc);
@@ -356,8 +390,14 @@ void free_local_plan(LocalPlan *lp) {
 
 // Passes for the full 2^n space of H, or nullptr when the operator does not fit
 // (a mask wider than the local set, too many passes, groups or terms).
-LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st) {
-    if (n < kLocBits + 1 || n > 40 || H->m == 0 || H->G == 0) return nullptr;
+namespace {
+LocalPlan *build_local_plan_cb(pauli_sum *H, int n, int cb, cudaStream_t st) {
+    // window of a pass: kLocBits bits in each CTA plus cb bits across the cluster;
+    // with a cluster the staged runs shrink to 16-32 bytes so that the run bits
+    // leave room for more bits of X masks
+    const int run = cb ? 1 : kLocRun;
+    const int wbits = kLocBits + cb;
+    if (n < wbits + 1 || n > 40 || H->m == 0 || H->G == 0) return nullptr;
     const int64_t M = H->m, G = H->G;
     if (M > (int64_t)kLocMaxTerms * kLocMaxPass) return nullptr;
     std::vector<uint64_t> z(M), gx(G);
@@ -373,19 +413,19 @@ LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st) {
     for (int64_t g = 0; g < G; ++g) order[g] = g;
     auto top = [](uint64_t v) { return v ? 63 - __builtin_clzll(v) : -1; };
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return top(gx[a]) < top(gx[b]); });
-    const uint64_t runmask = (1ull << kLocRun) - 1ull;
+    const uint64_t runmask = (1ull << run) - 1ull;
     std::vector<std::vector<int64_t>> pass_groups;
     std::vector<uint64_t> pass_mask;
     uint64_t cur = runmask;
     std::vector<int64_t> curg;
     for (int64_t g : order) {
         const uint64_t nm = cur | gx[g];
-        if (__builtin_popcountll(nm) <= kLocBits) {
+        if (__builtin_popcountll(nm) <= wbits) {
             cur = nm;
             curg.push_back(g);
             continue;
         }
-        if (__builtin_popcountll(runmask | gx[g]) > kLocBits) return nullptr;
+        if (__builtin_popcountll(runmask | gx[g]) > wbits) return nullptr;
         pass_groups.push_back(curg);
         pass_mask.push_back(cur);
         cur = runmask | gx[g];
@@ -398,22 +438,32 @@ LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st) {
     auto lp = new LocalPlan();
     lp->al = H->al;
     lp->n = n;
+    lp->run = run;
+    lp->cb = cb;
     lp->npass = (int)pass_groups.size();
-    std::vector<uint32_t> h_xloc, h_zloc, tab_z;
+    std::vector<uint32_t> h_xloc, h_zloc, tab_z, h_xcl;
     std::vector<int32_t> h_t0, h_tz;
-    std::vector<uint64_t> h_znl, h_hoff;
+    std::vector<uint64_t> h_znl, h_hoff, h_xnl;
     std::vector<double2> h_c, tab_c;
     int tab_b = 0;
     for (int p = 0; p < lp->npass; ++p) {
-        uint64_t L = pass_mask[p];
-        // fill the local set up to kLocBits with the lowest unused bits
-        for (int bit = 0; bit < n && __builtin_popcountll(L) < kLocBits; ++bit) L |= 1ull << bit;
-        std::vector<int> pos, hpos, npos;
+        uint64_t W = pass_mask[p];
+        // fill the window up to wbits with the lowest unused bits
+        for (int bit = 0; bit < n && __builtin_popcountll(W) < wbits; ++bit) W |= 1ull << bit;
+        // the cluster bits: the cb highest bits of the window above the run bits;
+        // L = the bits of one CTA's chunk
+        std::vector<int> clpos;
+        for (int bit = n - 1; bit >= run && (int)clpos.size() < cb; --bit)
+            if ((W >> bit) & 1ull) clpos.insert(clpos.begin(), bit);
+        uint64_t clmask = 0;
+        for (int bit : clpos) clmask |= 1ull << bit;
+        const uint64_t L = W & ~clmask;
+        std::vector<int> pos, hpos, npos(clpos);
         for (int bit = 0; bit < n; ++bit) {
             if ((L >> bit) & 1ull) {
                 pos.push_back(bit);
-                if (bit >= kLocRun) hpos.push_back(bit);
-            } else {
+                if (bit >= run) hpos.push_back(bit);
+            } else if (!((clmask >> bit) & 1ull)) {
                 npos.push_back(bit);
             }
         }
@@ -434,6 +484,8 @@ LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st) {
         for (int64_t g : pass_groups[p]) {
             const bool x0 = gx[g] == 0;  // the x = 0 group sorts first, so it leads pass 0
             h_xloc.push_back(compress(gx[g], pos));
+            h_xcl.push_back(compress(gx[g], clpos));
+            const uint64_t xnl = gx[g] & ~L;  // only cluster bits: x lies inside the window
             h_t0.push_back((int32_t)h_c.size());
             // terms with z_loc = 0 first (folded per chunk into one constant), then the
             // rest; the x = 0 group's terms with z_nl = 0 go to the table instead
@@ -453,12 +505,14 @@ LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st) {
             for (int64_t t : zero) {
                 h_zloc.push_back(0);
                 h_znl.push_back(z[t] & ~L);
+                h_xnl.push_back(xnl);
                 h_c.push_back(c[t]);
             }
             h_tz.push_back((int32_t)h_c.size());
             for (int64_t t : rest) {
                 h_zloc.push_back(compress(z[t], pos));
                 h_znl.push_back(z[t] & ~L);
+                h_xnl.push_back(xnl);
                 h_c.push_back(c[t]);
             }
             if (x0) {
@@ -483,6 +537,8 @@ LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st) {
     };
     try {
         lp->g_xloc = static_cast<uint32_t *>(up(h_xloc.data(), h_xloc.size() * sizeof(uint32_t)));
+        lp->g_xcl = static_cast<uint32_t *>(up(h_xcl.data(), h_xcl.size() * sizeof(uint32_t)));
+        lp->t_xnl = static_cast<uint64_t *>(up(h_xnl.data(), h_xnl.size() * sizeof(uint64_t)));
         lp->g_t0 = static_cast<int32_t *>(up(h_t0.data(), h_t0.size() * sizeof(int32_t)));
         lp->g_tz = static_cast<int32_t *>(up(h_tz.data(), h_tz.size() * sizeof(int32_t)));
         lp->t_zloc = static_cast<uint32_t *>(up(h_zloc.data(), h_zloc.size() * sizeof(uint32_t)));
@@ -510,6 +566,21 @@ LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st) {
     return lp;
 }
 
+}  // namespace
+
+// Passes for the full 2^n space of H, or nullptr when the operator does not fit
+// (a mask wider than the window, too many passes, groups or terms).  cluster:
+// windows of kLocBits + 3 bits shared by clusters of 8 CTAs (nullptr where the
+// device cannot launch clusters).
+LocalPlan *build_local_plan(pauli_sum *H, int n, bool cluster, cudaStream_t st) {
+    if (!cluster) return build_local_plan_cb(H, n, 0, st);
+    int dev = 0, ok = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_CUDA(cudaDeviceGetAttribute(&ok, cudaDevAttrClusterLaunch, dev));
+    if (!ok) return nullptr;
+    return build_local_plan_cb(H, n, kLocClusterBits, st);
+}
+
 int64_t local_last_chunks(const LocalPlan *lp) { return lp ? lp->pass[lp->npass - 1].nchunk : 0; }
 int64_t local_scratch_bytes(const LocalPlan *lp) { return lp ? lp->scratch_bytes : 0; }
 int local_passes(const LocalPlan *lp) { return lp ? lp->npass : 0; }
@@ -532,10 +603,14 @@ static void launch_local_r(LocalPlan *lp, const void *in, void *out, double *par
         P.g0 = Q.g0;
         P.g1 = Q.g1;
         P.diag = Q.diag;
+        P.run = lp->run;
+        P.cb = lp->cb;
         std::memcpy(P.npos, Q.npos, sizeof(P.npos));
         P.hoff = lp->hoff + Q.hoff_at;
         LocalArgs A;
         A.g_xloc = lp->g_xloc;
+        A.g_xcl = lp->g_xcl;
+        A.t_xnl = lp->t_xnl;
         A.g_t0 = lp->g_t0;
         A.g_tz = lp->g_tz;
         A.t_zloc = lp->t_zloc;
@@ -548,8 +623,26 @@ static void launch_local_r(LocalPlan *lp, const void *in, void *out, double *par
         const int flags = (p == 0 ? 1 : 8) | ((last && partials) ? 2 : 0);
         auto run = [&](auto kern) {
             smem_optin(reinterpret_cast<const void *>(kern), smem);
-            kern<<<(unsigned)Q.nchunk, kThreads, smem, st>>>(P, A, static_cast<const C2 *>(in),
-                                                              static_cast<C2 *>(out), partials, flags);
+            const C2 *pin = static_cast<const C2 *>(in);
+            C2 *pout = static_cast<C2 *>(out);
+            if (lp->cb == 0) {
+                kern<<<(unsigned)Q.nchunk, kThreads, smem, st>>>(P, A, pin, pout, partials, flags);
+            } else {
+                // clusters of 2^cb consecutive chunks: the same window, one cluster bit value each
+                cudaLaunchConfig_t lc = {};
+                lc.gridDim = dim3((unsigned)Q.nchunk, 1, 1);
+                lc.blockDim = dim3(kThreads, 1, 1);
+                lc.dynamicSmemBytes = smem;
+                lc.stream = st;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = 1u << lp->cb;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                lc.attrs = at;
+                lc.numAttrs = 1;
+                PS_CUDA(cudaLaunchKernelEx(&lc, kern, P, A, pin, pout, partials, flags));
+            }
             PS_LAUNCH_CHECK();
         };
         if (lp->real) run(k_apply_local<R, true, 4>);

@@ -82,7 +82,7 @@ extern "C" int pauli_expect_noalloc(pauli_sum *H, const pauli_sector *s, const v
         // dim-sized scratch, so that case needs hpsi_out or an existing scratch
         const ApplyCfg cfg = apply_config(*p, s->v, dtype, false);
         if (cfg.local && !hpsi_out)
-            PS_CHECK(local_scratch_bytes(p->local) >= (int64_t)bytes, PAULI_EUNSUPPORTED,
+            PS_CHECK(local_scratch_bytes(cfg.local_cl ? p->local_cl : p->local) >= (int64_t)bytes, PAULI_EUNSUPPORTED,
                      "pauli_expect_noalloc: this full-space operator is applied in passes that accumulate H psi in "
                      "a vector; pass hpsi_out (a dim-sized vector) or call pauli_expect once without it first");
         cudaStream_t cs = (cudaStream_t)st;

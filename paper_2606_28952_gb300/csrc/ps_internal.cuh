@@ -225,6 +225,7 @@ struct Plan {
     SvdPlan *svd = nullptr;
     // full-space passes over local bit sets (built on first use with a full sector)
     LocalPlan *local = nullptr;
+    LocalPlan *local_cl = nullptr;   // the same with windows shared by CTA clusters
     bool local_tried = false;
     // host copies of the item tables (list building)
     std::vector<uint32_t> h_it_xlo;
@@ -239,6 +240,7 @@ constexpr int kDiagTabBits = 12;
 // per chunk, the kLocRun lowest bits always local (runs of 8 contiguous amplitudes).
 constexpr int kLocBits = 13;
 constexpr int kLocRun = 3;
+constexpr int kLocClusterBits = 3;  // clustered windows: 8 CTAs, kLocBits + 3 bits
 constexpr int kLocMaxPass = 4;
 constexpr int kLocMaxTerms = 2048;
 constexpr int kLocMaxGroups = 512;
@@ -371,6 +373,7 @@ struct ApplyCfg {
     int64_t combine_nct = 0;
     bool direct = false;    // small plan: k_apply_direct (no staging, no split)
     bool local = false;     // full space: passes over local bit sets (local.cu)
+    bool local_cl = false;  // ... with the windows shared by CTA clusters (reported as ranked = 1)
     bool ranked = false;    // single block, rows staged by rank (KBLKR)
     bool list = false;      // single block, n_lo <= kListMaxLo: per-item lists of valid pairs (list.cu)
     bool svd = false;       // single block, real operator: SVD-factorised phases (svd.cu)
@@ -423,7 +426,7 @@ void launch_svd(const ApplyCfg &cfg, const Plan &p, const SectorView &v, const v
                 double *partials, cudaStream_t st);
 
 // local.cu
-LocalPlan *build_local_plan(pauli_sum *H, int n, cudaStream_t st);
+LocalPlan *build_local_plan(pauli_sum *H, int n, bool cluster, cudaStream_t st);
 void free_local_plan(LocalPlan *lp);
 int64_t local_last_chunks(const LocalPlan *lp);
 // bytes of the plan's H psi scratch (used when the caller passes no output vector)

@@ -183,6 +183,78 @@ def test_apply_local_passes(ps, dt, case):
             assert _rel(hp.cpu().numpy().astype(np.complex128), ref) <= TOL[dt]
 
 
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("case", ["xxz17", "lattice18"])
+def test_apply_local_cluster_passes(ps, dt, case):
+    """Windows of 16 bits shared by clusters of 8 CTAs (X masks on the cluster bits
+    read a peer's chunk through distributed shared memory), forced with
+    ranked = 1: apply and expect against the oracle."""
+    import torch
+    if case == "xxz17":
+        n = 17
+        x_, z_, cre, cim = w.xxz_terms(n, 1)
+        H = ps.PauliSum.from_terms(n, x_, z_, cre, cim)
+        R = oracle.build_sum(n, x_, z_, None, cre, cim)
+    else:
+        n = 18
+        x_, z_, cre, cim = _lattice_terms(n, 7)
+        H = ps.PauliSum.from_terms(n, x_, z_, cre, cim, form=ps.XZ)
+        R = oracle.build_sum(n, x_, z_, None, cre, cim, letter_form=False)
+    S = ps.Sector.full(n)
+    So = oracle.Sector.full(n)
+    ps.prepare(H, S)
+    c = ps.LaunchConfig(cols_per_thread=1, staged_rows=1, row_split=1, direct=2, ranked=1, ms=0.0)
+    ps.set_launch_config(H, S, _tdt(dt), c)
+    got = ps.launch_config(H, S, _tdt(dt))
+    assert got["direct"] == 2 and got["ranked"] == 1, got
+    psi = w.random_state(1 << n, 31)
+    x = _to_dev(psi, dt)
+    xin = x.cpu().numpy().astype(np.complex128)
+    ref = oracle.apply(So, R, xin)
+    out = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    assert _rel(out, ref) <= TOL[dt]
+    e_ref = np.vdot(xin, ref)
+    for hp in (None, torch.empty_like(x)):
+        r = ps.expect(H, S, x, hpsi_out=hp).cpu().numpy()
+        assert abs(complex(r[0], r[1]) - e_ref) <= TOL[dt] * np.linalg.norm(ref) * np.linalg.norm(xin)
+        if hp is not None:
+            assert _rel(hp.cpu().numpy().astype(np.complex128), ref) <= TOL[dt]
+    # the unclustered passes give the same vector
+    ps.set_launch_config(H, S, _tdt(dt), ps.LaunchConfig(cols_per_thread=1, staged_rows=1, row_split=1, direct=2,
+                                                         ranked=0, ms=0.0))
+    assert ps.launch_config(H, S, _tdt(dt))["ranked"] == 0
+    out2 = ps.apply(H, S, x).cpu().numpy().astype(np.complex128)
+    assert _rel(out2, out) <= 2 * TOL[dt]
+
+
+def test_apply_local_cluster_27_sites(ps):
+    """At 27 sites the clustered windows need 2 passes where 13-bit chunks need 3
+    (installed with ranked = 1; the plain passes stay the default); sampled rows
+    against the per-row oracle."""
+    import torch
+    n = 27
+    x_, z_, cre, cim = w.xxz_terms(n, 1)
+    H = ps.PauliSum.from_terms(n, x_, z_, cre, cim)
+    R = oracle.build_sum(n, x_, z_, None, cre, cim)
+    S = ps.Sector.full(n)
+    So = oracle.Sector.full(n)
+    ps.prepare(H, S)
+    assert ps.launch_config(H, S)["ranked"] == 0
+    ps.set_launch_config(H, S, torch.complex64, ps.LaunchConfig(cols_per_thread=4, staged_rows=1, row_split=1,
+                                                                direct=2, ranked=1, ms=0.0))
+    psi = w.random_state(1 << n, 37)
+    x = _to_dev(psi, "c64")
+    out = ps.apply(H, S, x)
+    cfg = ps.launch_config(H, S)
+    assert cfg["direct"] == 2 and cfg["ranked"] == 1, cfg
+    rows = np.random.default_rng(2).integers(0, 1 << n, 300)
+    rows = np.concatenate([rows, [0, 1, 7, 8, (1 << 16) - 1, 1 << 16, (1 << n) - 1]])
+    ref = oracle.apply_rows(So, R, x.cpu().numpy().astype(np.complex128), rows)
+    got = out.cpu().numpy().astype(np.complex128)[rows]
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, scale) * 10
+
+
 def test_apply_local_passes_24_sites_default(ps):
     """At 24 sites the pass scheme is the default launch of the full space (3 passes
     for the open chain); sampled rows against the per-row oracle."""
