@@ -129,6 +129,14 @@ void state_shape(pauli_batch *b, int i, int &tpt, int &nbuf, bool &ranked) {
     tpt = c.tpt >= 4 ? 4 : c.tpt;  // the batched kernel has 1, 2 or 4 columns per thread
     nbuf = c.nbuf;
     ranked = c.ranked;
+    // a pattern-staged row wider than 64 KB leaves one CTA per SM in a persistent
+    // launch (a single launch hides that behind its row split): stage by rank instead
+    const size_t es = b->dtype == PAULI_C64 ? 8 : 16;
+    if (!ranked && (es << v.n_lo) * (size_t)nbuf > 64 * 1024 && v.n_lo <= (v.irr ? 14 : 16)) {
+        ranked = true;
+        tpt = 4;
+        nbuf = 1;
+    }
 }
 
 // (Re)build the queue: shape groups (per state, or one uniform shape), states
