@@ -391,7 +391,9 @@ __device__ __forceinline__ uint32_t ranked_index(const RankTab &rt, uint32_t s) 
     return __popc(s) == rt.klo ? r : rt.dlo;
 }
 
-template <typename R, int KIND, bool REALH, int TPT>
+// NJ <= TPT: the columns j < NJ are evaluated (a warp whose last column lies
+// beyond the row runs with NJ = TPT - 1 and skips that column's work)
+template <typename R, int KIND, bool REALH, int TPT, int NJ = TPT>
 __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev &p, int q, const Buf<R> &B, int klo_req,
                                              const uint32_t (&tlo)[TPT], R (&accr)[TPT], R (&acci)[TPT],
                                              const RankTab &rt) {
@@ -401,14 +403,14 @@ __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev 
         const int4 e = B.item[it];
         uint32_t s[TPT];
 #pragma unroll
-        for (int j = 0; j < TPT; ++j) s[j] = tlo[j] ^ (uint32_t)e.x;
+        for (int j = 0; j < NJ; ++j) s[j] = tlo[j] ^ (uint32_t)e.x;
         R fr[TPT], fi[TPT];
         // the staged-row loads go out before the segment sums so that their
         // shared-memory latency overlaps them (24-qubit molecule 2.56 -> 2.52 ms,
         // 64 batched molecules 0.97 -> 0.90 s)
         C2 amp0[TPT];
 #pragma unroll
-        for (int j = 0; j < TPT; ++j) {
+        for (int j = 0; j < NJ; ++j) {
             fr[j] = R(0);
             fi[j] = R(0);
             amp0[j] = B.row[(KIND == KBLKR) ? ranked_index(rt, s[j]) : s[j]];
@@ -417,7 +419,7 @@ __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev 
             // x = 0 group: compensated FP32 summation of hi / lo coefficient pairs
             R er[TPT], ei[TPT];
 #pragma unroll
-            for (int j = 0; j < TPT; ++j) {
+            for (int j = 0; j < NJ; ++j) {
                 er[j] = R(0);
                 ei[j] = R(0);
             }
@@ -426,7 +428,7 @@ __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev 
                 const C2 a = B.a[sg];
                 const float2 l = B.alo[sg];
 #pragma unroll
-                for (int j = 0; j < TPT; ++j) {
+                for (int j = 0; j < NJ; ++j) {
                     const uint32_t par = __popc(z & s[j]);
                     float t, err;
                     two_sum(fr[j], flip((float)a.x, par), t, err);
@@ -440,7 +442,7 @@ __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev 
                 }
             }
 #pragma unroll
-            for (int j = 0; j < TPT; ++j) {
+            for (int j = 0; j < NJ; ++j) {
                 fr[j] += er[j];
                 fi[j] += ei[j];
             }
@@ -450,7 +452,7 @@ __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev 
                 const uint32_t z = B.z[sg];
                 const C2 a = B.a[sg];
 #pragma unroll
-                for (int j = 0; j < TPT; ++j) {
+                for (int j = 0; j < NJ; ++j) {
                     const uint32_t par = __popc(z & s[j]);
                     fr[j] += flip(a.x, par);
                     if (!REALH) fi[j] += flip(a.y, par);
@@ -458,7 +460,7 @@ __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev 
             }
         }
 #pragma unroll
-        for (int j = 0; j < TPT; ++j) {
+        for (int j = 0; j < NJ; ++j) {
             C2 amp = amp0[j];
             if (kind_multi(KIND) && kcls_lo<KIND>(v, s[j]) != klo_req) {
                 amp.x = R(0);
@@ -480,7 +482,7 @@ __device__ __forceinline__ void gather_piece(const SectorView &v, const PlanDev 
 // the piece's high-half phases into the segment coefficients itself (the same
 // loads across the CTA, served by L1) and reads psi from global memory: no
 // staging and no barrier.  Sources of a full space or of a single block only.
-template <typename R, int KIND, bool REALH, int TPT>
+template <typename R, int KIND, bool REALH, int TPT, int NJ = TPT>
 __device__ __forceinline__ void lofree_piece(const SectorView &v, const PlanDev &p, int q, uint32_t thi,
                                              const typename Cx<R>::T *__restrict__ psi, int64_t c0,
                                              const bool (&act)[TPT], const uint32_t (&tlo)[TPT], R (&accr)[TPT],
@@ -497,7 +499,7 @@ __device__ __forceinline__ void lofree_piece(const SectorView &v, const PlanDev 
     C2 amp[TPT];
     R fr[TPT], fi[TPT];
 #pragma unroll
-    for (int j = 0; j < TPT; ++j) {
+    for (int j = 0; j < NJ; ++j) {
         amp[j].x = R(0);
         amp[j].y = R(0);
         if (act[j]) amp[j] = psi[base + c0 + threadIdx.x + j * kThreads];
@@ -516,14 +518,14 @@ __device__ __forceinline__ void lofree_piece(const SectorView &v, const PlanDev 
         }
         const uint32_t z = __ldg(p.s_zlo + s);
 #pragma unroll
-        for (int j = 0; j < TPT; ++j) {
+        for (int j = 0; j < NJ; ++j) {
             const uint32_t par = __popc(z & tlo[j]);
             fr[j] += flip(ar, par);
             if (!REALH) fi[j] += flip(ai, par);
         }
     }
 #pragma unroll
-    for (int j = 0; j < TPT; ++j) {
+    for (int j = 0; j < NJ; ++j) {
         if (REALH) {
             accr[j] += fr[j] * amp[j].x;
             acci[j] += fr[j] * amp[j].y;
@@ -607,6 +609,10 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
         acci[j] = R(0);
     }
     __syncthreads();
+    // four columns a thread: a warp whose fourth column is past the row's end for
+    // every lane (e.g. D_lo = 924 against 1,024 slots) skips that column's work
+    constexpr int NJS = TPT == 4 ? 3 : TPT;
+    const bool short_warp = TPT == 4 && !__any_sync(0xffffffffu, act[TPT - 1]);
 
     const int pend = geo.split_p0[rc.split + 1];
     int q = next_piece<R, KIND>(v, p, geo.split_p0[rc.split] - 1, rc.thi, pend);
@@ -622,7 +628,8 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
                 cp_async_wait<0>();
             }
             __syncthreads();
-            gather_piece<R, KIND, REALH, TPT>(v, p, q, c ? B1 : B0, klo_req[c], tlo, accr, acci, rt);
+            if (short_warp) gather_piece<R, KIND, REALH, TPT, NJS>(v, p, q, c ? B1 : B0, klo_req[c], tlo, accr, acci, rt);
+            else gather_piece<R, KIND, REALH, TPT>(v, p, q, c ? B1 : B0, klo_req[c], tlo, accr, acci, rt);
             __syncthreads();
             c ^= 1;
             q = qn;
@@ -630,12 +637,14 @@ __device__ __forceinline__ void apply_unit(const SectorView &v, const Geom &geo,
     } else {
         while (q < pend) {
             if (!kind_multi(KIND) && __ldg(p.pc_lofree + q)) {
-                lofree_piece<R, KIND, REALH, TPT>(v, p, q, rc.thi, psi, rc.c0, act, tlo, accr, acci);
+                if (short_warp) lofree_piece<R, KIND, REALH, TPT, NJS>(v, p, q, rc.thi, psi, rc.c0, act, tlo, accr, acci);
+                else lofree_piece<R, KIND, REALH, TPT>(v, p, q, rc.thi, psi, rc.c0, act, tlo, accr, acci);
             } else {
                 stage_piece<R, KIND, REALH>(v, p, q, rc.thi, psi, B0, &klo_req[0]);
                 cp_async_wait<0>();
                 __syncthreads();
-                gather_piece<R, KIND, REALH, TPT>(v, p, q, B0, klo_req[0], tlo, accr, acci, rt);
+                if (short_warp) gather_piece<R, KIND, REALH, TPT, NJS>(v, p, q, B0, klo_req[0], tlo, accr, acci, rt);
+                else gather_piece<R, KIND, REALH, TPT>(v, p, q, B0, klo_req[0], tlo, accr, acci, rt);
                 __syncthreads();
             }
             q = next_piece<R, KIND>(v, p, q, rc.thi, pend);
