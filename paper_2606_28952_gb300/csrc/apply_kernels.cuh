@@ -309,10 +309,16 @@ __device__ __forceinline__ void stage_piece(const SectorView &v, const PlanDev &
             for (int64_t r = 2 * tid; r < len; r += 2 * nth) cp_async16(B.row + r, psi + base + r);
         }
     } else if (KIND == KBLKR) {
-        // dense copy of the source row, indexed later through the rank table
-        for (int64_t r = tid; r < len; r += nth) {
-            if (sizeof(C2) == 16) cp_async16(B.row + r, psi + base + r);
-            else cp_async8(B.row + r, psi + base + r);
+        // dense copy of the source row, indexed later through the rank table; on the
+        // complex64 path two amplitudes per 16-byte copy when the row starts on an
+        // even index (every row of an even-width block)
+        if (sizeof(C2) == 16) {
+            for (int64_t r = tid; r < len; r += nth) cp_async16(B.row + r, psi + base + r);
+        } else if ((base & 1) == 0) {
+            for (int64_t r = 2 * tid; r + 1 < len; r += 2 * nth) cp_async16(B.row + r, psi + base + r);
+            if ((len & 1) && tid == 0) cp_async8(B.row + len - 1, psi + base + len - 1);
+        } else {
+            for (int64_t r = tid; r < len; r += nth) cp_async8(B.row + r, psi + base + r);
         }
     } else {
         const uint32_t *lst = v.list_lo + loff;
