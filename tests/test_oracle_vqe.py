@@ -93,3 +93,41 @@ def test_pool_gradient_of_a_commuting_generator_is_zero():
     N = oracle.fermion_sum(2 * NORB, terms)
     psi = w.random_state(s.dim, 78)
     assert abs(vqe.pool_gradients(s, H, [N], psi)[0]) < 1e-12
+
+
+def test_pair_doubles_keep_the_seniority_zero_configurations():
+    """The reading behind the row-restricted energy of the 32-qubit scan: every
+    generalized pair double maps the configurations whose beta string equals the
+    alpha string onto themselves, so a product of them applied to the closed-shell
+    reference vanishes off that set, and <psi|H|psi> over the set equals the full
+    expectation (checked with the oracle's own apply)."""
+    norb, npair = 6, 3
+    s = oracle.Sector.molecular(norb, npair, npair)
+    cfg = s.configs()
+    sz = set(int(c) for c in w.seniority_zero_configs(norb, npair))
+    assert len(sz) == 20 and all(c in set(int(x) for x in cfg) for c in sz)
+    mask = np.array([int(c) in sz for c in cfg])
+    for p, q in w.pair_double_ansatz(norb, 15):
+        G = oracle.fermion_sum(2 * norb, w.pair_double_generator(norb, p, q))
+        for idx in np.flatnonzero(mask):
+            e = np.zeros(len(cfg), complex)
+            e[idx] = 1.0
+            out = oracle.apply(s, G, e)
+            assert np.abs(out[~mask]).max(initial=0.0) == 0.0, (p, q, int(cfg[idx]))
+    # a product state of the ansatz and its energy from the set alone
+    h0, h1, g0 = w.pes_integrals(norb, w.PES_SEED)
+    h, g = w.pes_point(h0, h1, g0, 1.7)
+    H = oracle.jw_hamiltonian(norb, h, g, eps_drop=1e-12)
+    gens = [oracle.fermion_sum(2 * norb, w.pair_double_generator(norb, p, q))
+            for p, q in w.pair_double_ansatz(norb, 15)]
+    ref = int(s.index(oracle.hf_config(norb, npair, npair))[0])
+    theta = np.random.default_rng(3).uniform(-0.5, 0.5, len(gens))
+    psi = np.zeros(len(cfg), complex)
+    psi[ref] = 1.0
+    for G, t in zip(gens, theta):
+        psi = oracle.rotate(s, G, t, psi)
+    assert np.abs(psi[~mask]).max() == 0.0
+    hp = oracle.apply(s, H, psi)
+    e_full = np.vdot(psi, hp).real
+    e_rows = np.vdot(psi[mask], hp[mask]).real
+    assert abs(e_full - e_rows) <= 1e-13 * max(1.0, abs(e_full))
