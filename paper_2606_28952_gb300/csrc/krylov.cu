@@ -11,7 +11,10 @@
 //   psi(t+dt) = beta_0 V_m exp(-i dt T_m) e_0,  T_m = tridiag(beta, alpha, beta),
 // with alpha_j from the FP64 reduction of the apply kernel (pauli_expect's
 // epilogue), FP64 norms, and exp(-i dt T_m) e_0 from a cyclic Jacobi
-// eigen-decomposition of the small real symmetric T_m on the device.
+// eigen-decomposition of the small real symmetric T_m on the device.  The
+// vectors are stored unnormalised, u_j = beta_j v_j (j > 0): their scales enter
+// the next update's coefficients and the final combination, so no pass over the
+// state rescales them.
 #include <cmath>
 #include <vector>
 
@@ -102,27 +105,39 @@ __global__ void __launch_bounds__(kVecThreads) k_normalize(const typename Cx<R>:
     }
 }
 
-// w <- w - alpha_j v_j - beta_j v_{j-1}; partial sums of ||w||^2.  alpha_j is the
-// real part of <v_j|H v_j> left in sc->red by the apply's expectation reduction.
+// 1 / beta_j, the scale of the stored Lanczos vector u_j (v_j = u_j / beta_j;
+// u_0 = v_0 is stored normalised)
+__device__ __forceinline__ double lanczos_scale(const KrylovScalars *sc, int j) {
+    if (j == 0) return 1.0;
+    const double b = sc->beta[j];
+    return b > 1e-300 ? 1.0 / b : 0.0;
+}
+
+// The Lanczos vectors are stored unnormalised (u_j = beta_j v_j for j > 0), which
+// saves the pass that would rescale each of them.  On entry w = H u_j; on exit
+//   w <- s_j (w - alpha_j u_j) - beta_j s_{j-1} u_{j-1} = H v_j - alpha_j v_j - beta_j v_{j-1}
+// (= u_{j+1}), with s_j = 1 / beta_j and alpha_j = s_j^2 Re <u_j|H u_j> from the
+// apply's FP64 expectation reduction left in sc->red; partial sums of ||w||^2.
 template <typename R>
 __global__ void __launch_bounds__(kVecThreads)
 k_lanczos_update(typename Cx<R>::T *__restrict__ w, const typename Cx<R>::T *__restrict__ vj,
                  const typename Cx<R>::T *__restrict__ vjm1, int64_t n, KrylovScalars *sc, int j,
                  double *partials) {
-    const double alpha = sc->red[0];
+    const double sj = lanczos_scale(sc, j);
+    const double alpha = sc->red[0] * sj * sj;
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->alpha[j] = alpha;
-    const R a = (R)alpha;
-    const R b = vjm1 ? (R)sc->beta[j] : R(0);
+    const R c1 = (R)sj, c2 = (R)(alpha * sj);
+    const R c3 = vjm1 ? (R)(sc->beta[j] * lanczos_scale(sc, j - 1)) : R(0);
     NormAcc<R> acc;
     for (int64_t i = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads) {
         typename Cx<R>::T x = w[i];
         const typename Cx<R>::T v = vj[i];
-        x.x -= a * v.x;
-        x.y -= a * v.y;
+        x.x = c1 * x.x - c2 * v.x;
+        x.y = c1 * x.y - c2 * v.y;
         if (vjm1) {
             const typename Cx<R>::T u = vjm1[i];
-            x.x -= b * u.x;
-            x.y -= b * u.y;
+            x.x -= c3 * u.x;
+            x.y -= c3 * u.y;
         }
         w[i] = x;
         acc.add(x);
@@ -233,7 +248,9 @@ __global__ void __launch_bounds__(kVecThreads) k_krylov_combine(const typename C
     __shared__ double cr[kMaxKrylov], ci[kMaxKrylov];
     __shared__ float4 c4[kMaxKrylov];
     if (threadIdx.x < m) {
-        const double a = sc->cre[threadIdx.x], b = sc->cim[threadIdx.x];
+        // psi = sum_j c_j v_j = sum_j (c_j s_j) u_j
+        const double sj = lanczos_scale(sc, threadIdx.x);
+        const double a = sc->cre[threadIdx.x] * sj, b = sc->cim[threadIdx.x] * sj;
         cr[threadIdx.x] = a;
         ci[threadIdx.x] = b;
         const float ah = (float)a, bh = (float)b;
@@ -252,7 +269,9 @@ __global__ void __launch_bounds__(kVecThreads) k_krylov_combine(const typename C
 }
 
 // k_reduce of apply.cu for the [nparts][4] partials (fixed order)
-__global__ void __launch_bounds__(1024) k_reduce4(const double *partials, int64_t nparts, double *result) {
+// beta_out (nullable): also sqrt(result[0]), the norm the sum of squares gives
+__global__ void __launch_bounds__(1024) k_reduce4(const double *partials, int64_t nparts, double *result,
+                                                  double *beta_out = nullptr) {
     __shared__ double sm[4][1024];
     const int t = threadIdx.x;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
@@ -266,6 +285,7 @@ __global__ void __launch_bounds__(1024) k_reduce4(const double *partials, int64_
         __syncthreads();
     }
     if (t < 4) result[t] = sm[t][0];
+    if (t == 0 && beta_out) *beta_out = sqrt(sm[0][0]);
 }
 
 }  // namespace
@@ -322,8 +342,9 @@ void krylov_step_t(pauli_krylov *k, void *psi_v, double dt, cudaStream_t st) {
         launch_reduce(p->partials, nparts, red, st);
         k_lanczos_update<R><<<nb, kVecThreads, 0, st>>>(w, vj, j > 0 ? V + (int64_t)(j - 1) * n : nullptr, n, k->sc,
                                                          j, k->partials);
-        k_reduce4<<<1, 1024, 0, st>>>(k->partials, nb, red);
-        if (j + 1 < k->m) k_normalize<R><<<nb, kVecThreads, 0, st>>>(w, w, n, k->sc, j + 1);
+        // beta_{j+1} = ||u_{j+1}||; u_{j+1} stays unnormalised (its scale enters the
+        // next update and the combination)
+        k_reduce4<<<1, 1024, 0, st>>>(k->partials, nb, red, k->sc->beta + j + 1);
         PS_LAUNCH_CHECK();
     }
     // beta_m of the last update is not needed by T_m; exp(-i dt T_m) e_0 and the combination
