@@ -447,6 +447,7 @@ ApplyCfg apply_config(const Plan &p, const SectorView &v, int dtype, bool allow_
             c.local = true;
             c.local_cl = cl;
             c.ranked = cl;
+            c.tpt = ch.tpt == 8 ? 8 : 4;  // targets per thread of the pass kernel
             c.direct = false;
             c.smem = 0;
             c.nbuf = 1;
@@ -540,7 +541,7 @@ void launch_apply(pauli_sum *H, const Plan &p, const SectorView &v, const void *
     if (cfg.nct == 0) return;
     PS_CHECK(cfg.nct < (1ll << 31), PAULI_EUNSUPPORTED, "apply: too many thread blocks");
     if (cfg.local) {
-        launch_local(cfg.local_cl ? p.local_cl : p.local, psi_in, psi_out, dtype, v.dim, partials, st);
+        launch_local(cfg.local_cl ? p.local_cl : p.local, psi_in, psi_out, dtype, v.dim, partials, cfg.tpt, st);
         return;
     }
     PS_CHECK(cfg.smem <= kMaxDynSmem, PAULI_EUNSUPPORTED,

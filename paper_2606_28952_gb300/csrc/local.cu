@@ -592,7 +592,7 @@ size_t local_smem(const LocalPlan *lp, int p, int dtype) {
 }
 
 template <typename R>
-static void launch_local_r(LocalPlan *lp, const void *in, void *out, double *partials, cudaStream_t st) {
+static void launch_local_r(LocalPlan *lp, const void *in, void *out, double *partials, int tpt, cudaStream_t st) {
     using C2 = typename Cx<R>::T;
     for (int p = 0; p < lp->npass; ++p) {
         const LocalPlan::Pass &Q = lp->pass[p];
@@ -645,12 +645,18 @@ static void launch_local_r(LocalPlan *lp, const void *in, void *out, double *par
             }
             PS_LAUNCH_CHECK();
         };
-        if (lp->real) run(k_apply_local<R, true, 4>);
-        else run(k_apply_local<R, false, 4>);
+        if (tpt == 8) {
+            if (lp->real) run(k_apply_local<R, true, 8>);
+            else run(k_apply_local<R, false, 8>);
+        } else {
+            if (lp->real) run(k_apply_local<R, true, 4>);
+            else run(k_apply_local<R, false, 4>);
+        }
     }
 }
 
-void launch_local(LocalPlan *lp, const void *in, void *out, int dtype, int64_t dim, double *partials, cudaStream_t st) {
+void launch_local(LocalPlan *lp, const void *in, void *out, int dtype, int64_t dim, double *partials, int tpt,
+                  cudaStream_t st) {
     const int64_t bytes = dim * (dtype == PAULI_C64 ? 8 : 16);
     if (!out) {
         if (lp->scratch_bytes < bytes) {
@@ -663,8 +669,8 @@ void launch_local(LocalPlan *lp, const void *in, void *out, int dtype, int64_t d
         }
         out = lp->scratch;
     }
-    if (dtype == PAULI_C64) launch_local_r<float>(lp, in, out, partials, st);
-    else launch_local_r<double>(lp, in, out, partials, st);
+    if (dtype == PAULI_C64) launch_local_r<float>(lp, in, out, partials, tpt, st);
+    else launch_local_r<double>(lp, in, out, partials, tpt, st);
 }
 
 }  // namespace ps

@@ -432,7 +432,8 @@ int64_t local_last_chunks(const LocalPlan *lp);
 // bytes of the plan's H psi scratch (used when the caller passes no output vector)
 int64_t local_scratch_bytes(const LocalPlan *lp);
 int local_passes(const LocalPlan *lp);
-void launch_local(LocalPlan *lp, const void *in, void *out, int dtype, int64_t dim, double *partials, cudaStream_t st);
+void launch_local(LocalPlan *lp, const void *in, void *out, int dtype, int64_t dim, double *partials, int tpt,
+                  cudaStream_t st);
 
 // linalg.cu: per-device scratch of FP64 partial sums shared by the reductions
 // that run on a fixed grid (pauli_vdot, pauli_rotate_adjoint)

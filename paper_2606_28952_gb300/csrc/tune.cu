@@ -115,13 +115,15 @@ int pauli_tune(pauli_sum *H, const pauli_sector *s, int dtype, int reps, pauli_l
         std::vector<LaunchChoice> cand;
         const bool fits = p.I <= 256 && p.S <= 1024;
         if (s->v.kind == PAULI_SECTOR_FULL)
-            for (int cl : {0, 1}) {
-                if (!(cl ? p.local_cl : p.local)) continue;
-                LaunchChoice c;
-                c.direct = 2;
-                c.ranked = cl;
-                cand.push_back(c);
-            }
+            for (int cl : {0, 1})
+                for (int tpt : {4, 8}) {
+                    if (!(cl ? p.local_cl : p.local)) continue;
+                    LaunchChoice c;
+                    c.direct = 2;
+                    c.ranked = cl;
+                    c.tpt = tpt;
+                    cand.push_back(c);
+                }
         if (v.kind == PAULI_SECTOR_BLOCKS && v.nblk == 1 && find_lists(p, v.klo[0]))
             for (int ns : {1, 2, 4, 8, 16}) {
                 if (ns > 1 && ns > std::max<int64_t>(1, p.P / 8)) continue;

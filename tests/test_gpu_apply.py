@@ -148,9 +148,11 @@ def _lattice_terms(n, seed):
 
 @pytest.mark.parametrize("dt", ["c128", "c64"])
 @pytest.mark.parametrize("case", ["xxz16", "lattice17"])
-def test_apply_local_passes(ps, dt, case):
+@pytest.mark.parametrize("tpt", [1, 8])
+def test_apply_local_passes(ps, dt, case, tpt):
     """The full space in passes over local bit sets (2 passes here, forced at this
-    size): apply and expect against the oracle, with and without the H psi output."""
+    size), 4 targets per thread (cols_per_thread 1: the default) or 8: apply and
+    expect against the oracle, with and without the H psi output."""
     import torch
     if case == "xxz16":
         n = 16
@@ -165,9 +167,10 @@ def test_apply_local_passes(ps, dt, case):
     S = ps.Sector.full(n)
     So = oracle.Sector.full(n)
     ps.prepare(H, S)
-    c = ps.LaunchConfig(cols_per_thread=1, staged_rows=1, row_split=1, direct=2, ranked=0, ms=0.0)
+    c = ps.LaunchConfig(cols_per_thread=tpt, staged_rows=1, row_split=1, direct=2, ranked=0, ms=0.0)
     ps.set_launch_config(H, S, _tdt(dt), c)
-    assert ps.launch_config(H, S, _tdt(dt))["direct"] == 2
+    got = ps.launch_config(H, S, _tdt(dt))
+    assert got["direct"] == 2 and got["cols_per_thread"] == (8 if tpt == 8 else 4), got
     psi = w.random_state(1 << n, 23)
     x = _to_dev(psi, dt)
     xin = x.cpu().numpy().astype(np.complex128)
