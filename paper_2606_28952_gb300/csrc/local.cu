@@ -11,6 +11,12 @@
 // passes add to it in a fixed order (no atomics); the last one also produces
 // the FP64 expectation partials.  The x = 0 group's terms without bits outside
 // L come from a table over L.
+//
+// Clustered windows (LocalPlan::cb = 3): a pass's window of kLocBits + 3 bits is
+// held by a cluster of 8 CTAs, each with the chunk of one value of the 3
+// cluster bits; a group whose X mask has cluster bits reads its sources from
+// the peer CTA's chunk through distributed shared memory.  Runs shrink to 2
+// amplitudes (16 bytes) so that a 30-site chain needs two passes instead of three.
 #include <algorithm>
 #include <cstring>
 #include <vector>

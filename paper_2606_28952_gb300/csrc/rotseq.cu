@@ -15,15 +15,19 @@
 //      between rotations; each pair {t, t ^ x} is updated by one thread),
 //   3. writes the tile back,
 // so psi is read and written once per run instead of once per rotation:
-//   ROW  runs (x_hi = 0, and diagonal generators): tile = one row;
+//   ROW  runs (x_hi = 0, and diagonal generators): tile = one or more rows;
 //   COL  runs (x_lo = 0, and diagonal generators): tile = every row of a
-//        block of a few adjacent columns (64-byte row segments);
+//        block of a few adjacent columns;
 //   PAIR runs (one common x_hi != 0, with row-local and diagonal generators):
-//        tile = the rows {r, r ^ x_hi} (or r alone when r ^ x_hi is outside
+//        tile = row pairs {r, r ^ x_hi} (or r alone when r ^ x_hi is outside
 //        the sector; such rows are skipped when no generator of the run acts
 //        inside one row).
-// Runs whose tile does not fit in shared memory (or sectors that are not one
-// product block) fall back to one pauli_rotate launch per generator.
+// When every generator of a run has tabulated active patterns and keeps the
+// sector, the pairs each one rotates are listed at creation and a tile visits
+// only those (k_rotseq_list); other runs test every amplitude of the tile
+// against every generator (k_rotseq).  Runs whose tile does not fit in shared
+// memory (or sectors that are not one product block) fall back to one
+// pauli_rotate launch per generator.
 #include <algorithm>
 #include <climits>
 #include <cmath>
