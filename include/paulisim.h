@@ -441,7 +441,12 @@ int pauli_mlp_adam_step(pauli_mlp *m, float lr, int t, pauli_stream_t st);
 
 /* steps x (pauli_mlp_backward + pauli_mlp_adam_step with t = t0+1 .. t0+steps)
  * in one call, enqueued on st; loss (device double, may be NULL) is that of
- * the last step's forward pass. */
+ * the last step's forward pass.  The first steps - 1 steps replay a CUDA graph
+ * of one step (captured on the handle's own stream on the first call and again
+ * whenever batch, x, target or lr change; ordered after and before st with
+ * events), the last one runs directly on st; the arithmetic is that of the
+ * eager steps.  Calls with one handle must be ordered; st must not itself be
+ * under stream capture. */
 int pauli_mlp_train(pauli_mlp *m, int batch, const float *x, const float *target, int steps, float lr, int t0,
                     double *loss, pauli_stream_t st);
 

@@ -145,6 +145,25 @@ __global__ void k_adam(int64_t n, float *w, const float *g, float *m, float *v, 
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// Adam with the bias corrections of the step (*step) of this training call taken
+// from a host-computed table c12 = {1 - b1^t, 1 - b2^t} per step (the same float
+// values as the eagerly launched k_adam gets), for the replayed graph of one step
+__global__ void k_adam_tab(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1, float b2,
+                           float eps, const float *c12, const int *step) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = *step;
+    const float c1 = c12[2 * s], c2 = c12[2 * s + 1];
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_step_inc(int *step) { ++*step; }
+
 __global__ void k_to_bf16(int64_t n, const float *src, __nv_bfloat16 *dst) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = __float2bfloat16(src[i]);
@@ -169,6 +188,17 @@ struct pauli_mlp {
           *dZ1 = nullptr;
     __nv_bfloat16 *H1b = nullptr, *H2b = nullptr, *dYb = nullptr, *dZ2b = nullptr;
     double *loss_rows = nullptr;
+    // one training step captured as a CUDA graph and replayed (pauli_mlp_train):
+    // the graph is keyed by the batch, the input / target pointers and lr
+    cudaGraphExec_t gexec = nullptr;
+    int g_batch = 0;
+    const float *g_x = nullptr, *g_t = nullptr;
+    float g_lr = 0.f;
+    float *c12 = nullptr;      // [c12_cap][2] bias corrections of the call's steps (device)
+    int c12_cap = 0;
+    int *d_step = nullptr;     // the step being replayed (device)
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -220,12 +250,55 @@ void mlp_backward(pauli_mlp *p, int batch, const float *x, const float *target, 
     PS_LAUNCH_CHECK();
 }
 
+constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
+
+void adam_corrections(int t, float &c1, float &c2) {
+    c1 = 1.f - std::pow(kAdamB1, (float)t);
+    c2 = 1.f - std::pow(kAdamB2, (float)t);
+}
+
 void mlp_adam(pauli_mlp *p, float lr, int t, cudaStream_t cs) {
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - std::pow(b1, (float)t), c2 = 1.f - std::pow(b2, (float)t);
-    k_adam<<<nb(p->np), 256, 0, cs>>>(p->np, p->w, p->g, p->m, p->v, lr, b1, b2, 1e-8f, c1, c2);
+    float c1, c2;
+    adam_corrections(t, c1, c2);
+    k_adam<<<nb(p->np), 256, 0, cs>>>(p->np, p->w, p->g, p->m, p->v, lr, kAdamB1, kAdamB2, kAdamEps, c1, c2);
     PS_LAUNCH_CHECK();
     mlp_refresh_bf16(p, cs);
+}
+
+void free_train_graph(pauli_mlp *p) {
+    if (p->gexec) (void)cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+}
+
+// One step (forward, backward, Adam from the table, bf16 refresh, step counter)
+// captured on the private stream; replayed steps - 1 times by pauli_mlp_train.
+void capture_train_step(pauli_mlp *p, int batch, const float *x, const float *target, float lr) {
+    free_train_graph(p);
+    cudaGraph_t graph = nullptr;
+    PS_CUDA(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+    try {
+        mlp_backward(p, batch, x, target, nullptr, p->gstream);
+        k_adam_tab<<<nb(p->np), 256, 0, p->gstream>>>(p->np, p->w, p->g, p->m, p->v, lr, kAdamB1, kAdamB2, kAdamEps,
+                                                      p->c12, p->d_step);
+        mlp_refresh_bf16(p, p->gstream);
+        k_step_inc<<<1, 1, 0, p->gstream>>>(p->d_step);
+    } catch (...) {
+        cudaGraph_t g = nullptr;
+        (void)cudaStreamEndCapture(p->gstream, &g);
+        if (g) (void)cudaGraphDestroy(g);
+        throw;
+    }
+    PS_CUDA(cudaStreamEndCapture(p->gstream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&p->gexec, graph, 0);
+    (void)cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        p->gexec = nullptr;
+        throw Error{PAULI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
+    }
+    p->g_batch = batch;
+    p->g_x = x;
+    p->g_t = target;
+    p->g_lr = lr;
 }
 
 template <typename F>
@@ -378,10 +451,45 @@ int pauli_mlp_train(pauli_mlp *p, int batch, const float *x, const float *target
         PS_CHECK(steps >= 0 && t0 >= 0 && (int64_t)t0 + steps < (1ll << 30), PAULI_EINVAL, "bad steps / t0");
         PS_CHECK(std::isfinite(lr) && lr > 0.f, PAULI_EINVAL, "lr must be positive");
         cudaStream_t cs = (cudaStream_t)st;
-        for (int s = 0; s < steps; ++s) {
-            mlp_backward(p, batch, x, target, s + 1 == steps ? loss : nullptr, cs);
-            mlp_adam(p, lr, t0 + s + 1, cs);
+        if (steps == 0) return;
+        // the first steps - 1 steps replay a captured graph of one step on the private
+        // stream, ordered after and before the caller's stream with events; the last
+        // step runs eagerly (it also reduces the loss).  The arithmetic is that of the
+        // eager steps: the same kernels, the same host-computed bias corrections.
+        const int ng = steps - 1;
+        if (ng > 0) {
+            if (!p->gstream) {
+                PS_CUDA(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+                PS_CUDA(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+                PS_CUDA(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
+                p->d_step = static_cast<int *>(dev_alloc(p->al, sizeof(int)));
+            }
+            if (p->c12_cap < ng) {
+                PS_CUDA(cudaStreamSynchronize(cs));
+                PS_CUDA(cudaStreamSynchronize(p->gstream));
+                free_train_graph(p);  // the graph holds the table's address
+                dev_free(p->al, p->c12);
+                p->c12 = nullptr;
+                p->c12_cap = 0;
+                p->c12 = static_cast<float *>(dev_alloc(p->al, (size_t)2 * ng * sizeof(float)));
+                p->c12_cap = ng;
+            }
+            std::vector<float> c12((size_t)2 * ng);
+            for (int s = 0; s < ng; ++s) adam_corrections(t0 + s + 1, c12[2 * s], c12[2 * s + 1]);
+            PS_CUDA(cudaEventRecord(p->ev_in, cs));
+            PS_CUDA(cudaStreamWaitEvent(p->gstream, p->ev_in, 0));
+            // pageable sources: the copies are staged before they return
+            PS_CUDA(cudaMemcpyAsync(p->c12, c12.data(), c12.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                    p->gstream));
+            PS_CUDA(cudaMemsetAsync(p->d_step, 0, sizeof(int), p->gstream));
+            if (!p->gexec || p->g_batch != batch || p->g_x != x || p->g_t != target || p->g_lr != lr)
+                capture_train_step(p, batch, x, target, lr);
+            for (int s = 0; s < ng; ++s) PS_CUDA(cudaGraphLaunch(p->gexec, p->gstream));
+            PS_CUDA(cudaEventRecord(p->ev_out, p->gstream));
+            PS_CUDA(cudaStreamWaitEvent(cs, p->ev_out, 0));
         }
+        mlp_backward(p, batch, x, target, loss, cs);
+        mlp_adam(p, lr, t0 + steps, cs);
     });
 }
 
@@ -391,8 +499,13 @@ int pauli_mlp_destroy(pauli_mlp *p) {
         set_error("not a valid pauli_mlp handle");
         return PAULI_EINVAL;
     }
+    if (p->gstream) (void)cudaStreamSynchronize(p->gstream);
+    free_train_graph(p);
+    if (p->gstream) (void)cudaStreamDestroy(p->gstream);
+    if (p->ev_in) (void)cudaEventDestroy(p->ev_in);
+    if (p->ev_out) (void)cudaEventDestroy(p->ev_out);
     void *bufs[] = {p->w, p->g, p->m, p->v, p->W2b, p->W3b, p->H1, p->H2, p->Y, p->dY, p->dH2, p->dZ2, p->dH1,
-                    p->dZ1, p->H1b, p->H2b, p->dYb, p->dZ2b, p->loss_rows};
+                    p->dZ1, p->H1b, p->H2b, p->dYb, p->dZ2b, p->loss_rows, p->c12, p->d_step};
     for (void *b : bufs) dev_free(p->al, b);
     p->magic = 0;
     delete p;

@@ -231,15 +231,21 @@ def test_mlp_adam_step_matches_oracle(ps):
 
 
 def test_mlp_train_call_equals_single_steps(ps):
-    """pauli_mlp_train(steps) runs exactly the kernels of steps x (backward + adam)."""
+    """pauli_mlp_train(steps) runs exactly the kernels of steps x (backward + adam),
+    its first steps - 1 steps from a replayed graph: bit for bit the single steps,
+    also on a second call that outgrows the first call's table (graph captured
+    again) and a third with another learning rate."""
     net_a, p, x, T, xd, Td = _mlp_case(ps, 1, 64, 20, 12, 5)
     net_b, *_ = _mlp_case(ps, 1, 64, 20, 12, 5)
-    la = net_a.train(xd, Td, 7, 3e-3, 0)
-    for t in range(1, 8):
-        lb = net_b.backward(xd, Td)
-        net_b.adam_step(3e-3, t)
-    assert np.array_equal(net_a.get_params(), net_b.get_params())
-    assert la.item() == lb.item()
+    t = 0
+    for steps, lr in ((7, 3e-3), (12, 3e-3), (5, 1e-3)):
+        la = net_a.train(xd, Td, steps, lr, t)
+        for _ in range(steps):
+            t += 1
+            lb = net_b.backward(xd, Td)
+            net_b.adam_step(lr, t)
+        assert np.array_equal(net_a.get_params(), net_b.get_params()), (steps, lr)
+        assert la.item() == lb.item()
 
 
 def test_mlp_training_fits_a_smooth_map(ps):
