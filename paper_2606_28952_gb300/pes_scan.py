@@ -87,7 +87,7 @@ def compare(prev, warm, min_train: int, target: float = TARGET):
 
 
 def run(norb: int = 8, npoints: int = 40, count: int = 200, dtype: str = "c128", seed: int | None = None,
-        min_train: int = 3, fit_steps: int = 1500, lr: float = 1e-3, maxiter: int = 300, ftol: float = 1e-10,
+        min_train: int = 3, fit_steps: int = 150, lr: float = 1e-3, maxiter: int = 300, ftol: float = 1e-10,
         window: int = 10, log=None, support: bool = False):
     import torch
     import workloads as w
@@ -132,7 +132,8 @@ def main(argv=None):
     ap.add_argument("--count", type=int, default=200)
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--min-train", type=int, default=3)
-    ap.add_argument("--fit-steps", type=int, default=1500)
+    ap.add_argument("--fit-steps", type=int, default=150,
+                    help="Adam steps per refit (the network is refit from its previous weights after each point)")
     ap.add_argument("--maxiter", type=int, default=300)
     ap.add_argument("--window", type=int, default=10)
     ap.add_argument("--rows", action="store_true", help="include the per-point rows")

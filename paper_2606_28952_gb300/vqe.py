@@ -451,7 +451,7 @@ def iterations_to(res: PointResult, E_target: float):
 
 
 def scan(make_problem, points, n_theta: int, warm: WarmStart | None = None, min_train: int = 3,
-         fit_steps: int = 1500, lr: float = 1e-3, opt=None, log=None, reuse=()):
+         fit_steps: int = 150, lr: float = 1e-3, opt=None, log=None, reuse=()):
     """Optimise the ansatz at each point in order.  Without ``warm`` every point
     starts from the previous point's converged angles.  With it, once
     min_train points are known, the energies of the network's start
