@@ -261,6 +261,9 @@ def run_ours(args, rank, world, local_rank):
     install_launch(ps, H, S, tdt, args.launch)
     x_can, _, _ = H.export()
     U = count_updates(x_can, 12, 12, 6, 6)
+    # group-level count U_g = sum_g #{t in S : t ^ x_g in S}: one source amplitude read per
+    # (target, group) pair that has a contribution
+    U_g = count_updates(np.unique(np.asarray(x_can, dtype=np.uint64)), 12, 12, 6, 6)
     psi_np = w.random_state(S.dim, w.MOL24.psi_seed)
     psi = torch.from_numpy(psi_np).to(dev, tdt)
     out = torch.empty_like(psi)
@@ -413,6 +416,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "alu", "achieved": achieved_gups, "peak": popc_peak, "unit": "Gupd/s",
                          "frac": achieved_gups / popc_peak,
                          "eff_hbm": achieved_gbs / hbm_peak, "eff_hbm_achieved_gbs": achieved_gbs,
+                         "gather_gbs": U_g * esize / t_step / 1e9, "gather_pairs_per_apply": U_g,
                          "eff_hbm_compulsory_bytes": alg_bytes, "eff_hbm_peak_gbs": hbm_peak,
                          "traffic": profiled_traffic("k_apply_mol24_c64.json") if args.dtype == "c64" else None,
                          "note": (f"updates U={U} per launch / CUDA-event step time (the step is the gather "
