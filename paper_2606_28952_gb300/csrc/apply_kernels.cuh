@@ -50,6 +50,14 @@ __device__ __forceinline__ double flip(double a, uint32_t parity_word) {
     return __hiloint2double((int)((uint32_t)__double2hiint(a) + (parity_word << 31)), __double2loint(a));
 }
 
+// acc += f a for a real f: one packed FP32x2 FMA on the complex64 path (the same
+// two fused multiply-adds as the scalar form)
+__device__ __forceinline__ void fma_real(float2 &acc, float f, float2 a) { acc = __ffma2_rn(make_float2(f, f), a, acc); }
+__device__ __forceinline__ void fma_real(double2 &acc, double f, double2 a) {
+    acc.x = fma(f, a.x, acc.x);
+    acc.y = fma(f, a.y, acc.y);
+}
+
 constexpr int kMaxSplit = 16;
 
 struct Geom {
@@ -885,25 +893,44 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
     }
     uint32_t tlo[TPT];
     bool act[TPT];
-    R accr[TPT], acci[TPT];
+    C2 acc[TPT];
 #pragma unroll
     for (int j = 0; j < TPT; ++j) {
         const int64_t c = rc.c0 + tid + j * kThreads;
         act[j] = c < rc.dlo;
         tlo[j] = 0;
         if (act[j]) tlo[j] = (KIND == KFULL) ? (uint32_t)c : __ldg(v.list_lo + v.lst_lo_off[rc.blk] + c);
-        accr[j] = R(0);
-        acci[j] = R(0);
+        acc[j].x = R(0);
+        acc[j].y = R(0);
     }
     __syncthreads();
     // phase 2: gather from global memory
     const bool full_tile = rc.c0 + (int64_t)TPT * kThreads <= rc.dlo;  // every column of the tile exists
+    const int own_cls = KIND == KFULL ? 0 : v.klo[rc.blk];             // low-half class of this row's columns
     for (int it = 0; it < p.I; ++it) {
         const DItem e = sm_it[it];
         if (e.klo < 0) continue;
         uint32_t s[TPT];
         C2 amp[TPT];
-        if (KIND == KFULL) {
+        // x_lo = 0 on a block sector: the source column is the target's own.  Within the
+        // same low-half class its rank is the column index (no class test, no rank
+        // lookup); in another class no column of this row has a source in the block.
+        // (real coefficients only: on the complex path the extra branch costs spills)
+        const bool same_col = REALH && KIND != KFULL && e.xlo == 0u;
+        if (same_col && e.klo != own_cls) continue;
+        if (same_col) {
+            const C2 *src = psi + (e.base + rc.c0 + tid);
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                s[j] = tlo[j];
+                if (act[j]) {
+                    amp[j] = src[j * kThreads];
+                } else {
+                    amp[j].x = R(0);
+                    amp[j].y = R(0);
+                }
+            }
+        } else if (KIND == KFULL) {
             // full space: the source row is contiguous; 32-bit offsets into it
             const C2 *src = psi + e.base;
 #pragma unroll
@@ -920,12 +947,12 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
                     }
             }
         } else {
+            const C2 *src = psi + e.base;  // the source row; 32-bit ranks into it
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
                 s[j] = tlo[j] ^ e.xlo;
                 const bool ok = act[j] && (kcls_lo<KIND>(v, s[j]) == e.klo);
-                const int64_t idx = e.base + (ok ? (int64_t)__ldg(v.rank_lo + s[j]) : 0);
-                amp[j] = psi[idx];
+                amp[j] = src[ok ? __ldg(v.rank_lo + s[j]) : 0u];
                 if (!ok) {
                     amp[j].x = R(0);
                     amp[j].y = R(0);
@@ -994,11 +1021,10 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
                 if (REALH) {
-                    accr[j] += fr[j] * amp[j].x;
-                    acci[j] += fr[j] * amp[j].y;
+                    fma_real(acc[j], fr[j], amp[j]);
                 } else {
-                    accr[j] += fr[j] * amp[j].x - fi[j] * amp[j].y;
-                    acci[j] += fr[j] * amp[j].y + fi[j] * amp[j].x;
+                    acc[j].x += fr[j] * amp[j].x - fi[j] * amp[j].y;
+                    acc[j].y += fr[j] * amp[j].y + fi[j] * amp[j].x;
                 }
             }
             continue;
@@ -1056,11 +1082,10 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
             if (REALH) {
-                accr[j] += fr[j] * amp[j].x;
-                acci[j] += fr[j] * amp[j].y;
+                fma_real(acc[j], fr[j], amp[j]);
             } else {
-                accr[j] += fr[j] * amp[j].x - fi[j] * amp[j].y;
-                acci[j] += fr[j] * amp[j].y + fi[j] * amp[j].x;
+                acc[j].x += fr[j] * amp[j].x - fi[j] * amp[j].y;
+                acc[j].y += fr[j] * amp[j].y + fi[j] * amp[j].x;
             }
         }
     }
@@ -1070,13 +1095,8 @@ k_apply_direct(SectorView v, Geom geo, PlanDev p, const typename Cx<R>::T *__res
     for (int j = 0; j < TPT; ++j) {
         if (!act[j]) continue;
         const int64_t idx = rc.own_base + rc.c0 + tid + j * kThreads;
-        if (flags & 1) {
-            C2 o;
-            o.x = accr[j];
-            o.y = acci[j];
-            out[idx] = o;
-        }
-        if (flags & 2) ea.add(psi[idx], accr[j], acci[j]);
+        if (flags & 1) out[idx] = acc[j];
+        if (flags & 2) ea.add(psi[idx], acc[j].x, acc[j].y);
     }
     if (flags & 2) {
         double er = ea.get(0), ei = ea.get(1), h2 = ea.get(2), p2 = ea.get(3);

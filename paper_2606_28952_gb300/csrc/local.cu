@@ -71,13 +71,6 @@ __device__ __forceinline__ double2 ld_tab<double>(const LocalArgs &a, uint32_t l
     return __ldg(a.dtab64 + l);
 }
 
-// acc += f a for a real f: one packed FP32x2 FMA on the complex64 path
-__device__ __forceinline__ void acc_real(float2 &acc, float f, float2 a) { acc = __ffma2_rn(make_float2(f, f), a, acc); }
-__device__ __forceinline__ void acc_real(double2 &acc, double f, double2 a) {
-    acc.x = fma(f, a.x, acc.x);
-    acc.y = fma(f, a.y, acc.y);
-}
-
 template <typename R, bool REALH, int TPT>
 __global__ void __launch_bounds__(kThreads)
 k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__ psi,
@@ -233,7 +226,7 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
                 for (int j = 0; j < TPT; ++j) {
                     const uint32_t sb = tb[j] ^ xb;
                     const R f = a0.x + flip(c, __popc(z & sb));
-                    acc_real(acc2[j], f, *reinterpret_cast<const C2 *>(src + sb));
+                    fma_real(acc2[j], f, *reinterpret_cast<const C2 *>(src + sb));
                 }
                 return;
             }
@@ -259,7 +252,7 @@ k_apply_local(LocalPassDev P, LocalArgs A, const typename Cx<R>::T *__restrict__
             for (int j = 0; j < TPT; ++j) {
                 const C2 amp = *reinterpret_cast<const C2 *>(src + sb[j]);
                 if (REALH) {
-                    acc_real(acc2[j], fr[j], amp);
+                    fma_real(acc2[j], fr[j], amp);
                 } else {
                     acc2[j].x += fr[j] * amp.x - fi[j] * amp.y;
                     acc2[j].y += fr[j] * amp.y + fi[j] * amp.x;

@@ -5,6 +5,9 @@
   pattern- vs rank-staged rows, staged rows in flight, row splits, the list
   gather, and the direct gather on a small lattice operator; the shape that
   actually ran is read back and checked;
+* the direct gather on a fixed-N sector of several blocks, with an operator
+  whose strings keep a row in its block, move it to another block, or leave
+  the sector;
 * the 32-qubit (8a,8b) sector (D = 165,636,900) with its default shape (rows
   staged by rank, 8 columns per thread) on sampled target rows;
 * the 64-molecule persistent batch at full size (8-14 orbitals) with the
@@ -17,6 +20,7 @@ relative error of the sampled H psi entries <= 1e-12 (complex128) and 1e-5
 (complex64).  The oracle's per-target definition runs in host threads (its C
 calls release the interpreter lock)."""
 import concurrent.futures as cf
+import math
 import os
 
 import numpy as np
@@ -161,6 +165,68 @@ def test_direct_gather_shapes(ps, dt, kind):
             assert _rel(out, ref) <= TOL[dt], (tpt, direct)
             r = ps.expect(H, S, xt).cpu().numpy()
             assert abs(complex(r[0], r[1]) - Eref) <= (1e-12 if dt == "c128" else 1e-5) * max(1.0, abs(Eref))
+
+
+def _block_changing_terms(n, n_lo, seed, real):
+    """XZ-form strings whose X masks lie in the high half only (one bit: the row
+    moves to a block of another low-half class, where no column of the target's
+    row has a source; two bits: it stays in its class and the source column is the
+    target's own), in the low half only, or in both, with random Z masks, plus
+    diagonal strings."""
+    rng = np.random.default_rng(seed)
+    hi_bits = np.arange(n_lo, n)
+    xs, zs, cre, cim = [], [], [], []
+
+    def add(xm, k):
+        for _ in range(k):
+            xs.append(xm)
+            zs.append(int(rng.integers(0, 1 << n)))
+            cre.append(rng.normal())
+            cim.append(0.0 if real else rng.normal())
+
+    add(0, 6)
+    for _ in range(6):
+        add(1 << int(rng.choice(hi_bits)), 2)
+    for _ in range(6):
+        a, b = rng.choice(hi_bits, 2, replace=False)
+        add((1 << int(a)) | (1 << int(b)), 2)
+    for _ in range(6):
+        add(int(rng.integers(1, 1 << n_lo)), 2)
+    for _ in range(6):
+        add(int(rng.integers(1, 1 << n_lo)) | (1 << int(rng.choice(hi_bits))), 2)
+    return np.array(xs, np.uint64), np.array(zs, np.uint64), np.array(cre), np.array(cim)
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+@pytest.mark.parametrize("real", [True, False])
+def test_direct_gather_block_changes(ps, dt, real):
+    """The direct gather on a fixed-N sector of several blocks (20 qubits, N = 10,
+    12 low bits: rows of up to 924 columns, several column tiles at one column a
+    thread), every columns-per-thread value, against the oracle and the staged gather."""
+    import torch
+    n, n_lo, N = 20, 12, 10
+    x_, z_, cre, cim = _block_changing_terms(n, n_lo, 31 + int(real), real)
+    H = ps.PauliSum.from_terms(n, x_, z_, cre, cim, form=ps.XZ)
+    R = oracle.build_sum(n, x_, z_, None, cre, cim, letter_form=False)
+    blocks = [(k, N - k) for k in range(N + 1) if k <= n_lo and N - k <= n - n_lo]
+    S = ps.Sector(n, ps.BLOCKS, n_lo, blocks)
+    So = oracle.Sector(n, oracle.BLOCKS, n_lo, blocks)
+    assert S.dim == So.dim == math.comb(n, N)
+    psi = _rounded(w.random_state(S.dim, 23), dt)
+    ref = oracle.apply(So, R, psi)
+    E = complex(np.vdot(psi, ref))
+    ps.prepare(H, S)
+    xt = torch.from_numpy(psi).to("cuda", _tdt(dt))
+    for tpt in (1, 2, 4):
+        for direct in (1, 0):
+            c = ps.LaunchConfig(cols_per_thread=tpt, staged_rows=1, row_split=1, direct=direct, ranked=0, ms=0.0)
+            ps.set_launch_config(H, S, _tdt(dt), c)
+            got = ps.launch_config(H, S, _tdt(dt))
+            assert got["direct"] == direct and got["cols_per_thread"] == tpt, got
+            out = ps.apply(H, S, xt).cpu().numpy().astype(np.complex128)
+            assert _rel(out, ref) <= TOL[dt], (tpt, direct)
+            r = ps.expect(H, S, xt).cpu().numpy()
+            assert abs(complex(r[0], r[1]) - E) <= (1e-12 if dt == "c128" else 1e-5) * max(1.0, abs(E)), (tpt, direct)
 
 
 # ----------------------------------------------------------------------------
