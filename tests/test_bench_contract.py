@@ -39,6 +39,23 @@ def test_update_count_matches_enumeration():
         H = oracle.jw_hamiltonian(norb, h, g, eps_drop=1e-12)
         x = np.asarray(H.x, dtype=np.uint64)
         assert count_updates(x, norb, norb, na, nb) == _brute_force_updates(norb, na, nb, x)
+        # the group-level count U_g behind the gather rate: one source read per
+        # (target, group) pair with a contribution
+        xg = np.unique(x)
+        assert count_updates(xg, norb, norb, na, nb) == _brute_force_updates(norb, na, nb, xg)
+
+
+def test_update_counts_of_the_12_qubit_molecule():
+    """6 orbitals, (3a,3b), D = 400: U = 400 * 907 term updates and U_g = 400 * 118
+    group updates (907 terms and 118 groups with a source in the sector per target on
+    average), the counts behind the metric and the gather rate."""
+    sys.path.insert(0, ROOT)
+    from bench import count_updates
+    h, g = w.MOL12.integrals()
+    H = oracle.jw_hamiltonian(6, h, g, eps_drop=1e-12)
+    x = np.asarray(H.x, dtype=np.uint64)
+    assert count_updates(x, 6, 6, 3, 3) == 400 * 907
+    assert count_updates(np.unique(x), 6, 6, 3, 3) == 400 * 118
 
 
 def test_reference_arm_prints_the_contract_line():
