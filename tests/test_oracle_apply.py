@@ -1,4 +1,5 @@
-"""Pins of the oracle's operator-state products against dense Kronecker-built matrices."""
+"""Pins of the oracle's operator-state products against dense Kronecker-built matrices
+and against closed-form free-fermion spectra of lattice chains."""
 import math
 
 import numpy as np
@@ -218,3 +219,69 @@ def test_low_mask_merge_needs_a_single_block():
     phi = w.random_state(S1.dim, 4)
     a, b = oracle.apply(S1, R, phi), oracle.apply(S1, Rm, phi)
     assert np.linalg.norm(a - b) <= 1e-13 * max(np.linalg.norm(a), 1.0)
+
+
+# ----------------------------------------------------------------------------
+# lattice models with a free-fermion (Jordan-Wigner) solution: closed-form
+# spectra that owe nothing to Kronecker products or to the oracle
+# ----------------------------------------------------------------------------
+def _dense_from_apply(So, R):
+    D = So.dim
+    M = np.zeros((D, D), complex)
+    for j in range(D):
+        e = np.zeros(D, complex)
+        e[j] = 1.0
+        M[:, j] = oracle.apply(So, R, e)
+    return M
+
+
+def test_transverse_field_ising_spectrum_is_free_fermion():
+    """Open transverse-field Ising chain of eq. TFIM with site-dependent couplings,
+    H = sum_i J_i Z_i Z_i+1 + sum_i h_i X_i.  A Jordan-Wigner transformation makes
+    it quadratic in fermions: its 2^n eigenvalues are sum_k +-L_k over all sign
+    choices, with L_k the singular values of the bidiagonal matrix of h (diagonal)
+    and J (superdiagonal) (Lieb, Schultz and Mattis 1961; Pfeuty 1970)."""
+    import itertools
+    n = 8
+    rng = np.random.default_rng(21)
+    J, h = rng.normal(size=n - 1), rng.normal(size=n)
+    xs, zs, cs = [], [], []
+    for i in range(n - 1):
+        xs.append(0); zs.append((1 << i) | (1 << (i + 1))); cs.append(J[i])
+    for i in range(n):
+        xs.append(1 << i); zs.append(0); cs.append(h[i])
+    c = np.array(cs)
+    R = oracle.build_sum(n, np.array(xs, np.uint64), np.array(zs, np.uint64), None, c, np.zeros_like(c))
+    M = _dense_from_apply(oracle.Sector.full(n), R)
+    assert np.abs(M - M.conj().T).max() == 0.0
+    L = np.linalg.svd(np.diag(h) + np.diag(J, 1), compute_uv=False)
+    spec = np.sort([np.dot(sg, L) for sg in itertools.product((-1.0, 1.0), repeat=n)])
+    assert np.abs(np.sort(np.linalg.eigvalsh(M)) - spec).max() <= 1e-12 * np.abs(L).sum()
+
+
+def test_xx_chain_spectra_per_particle_number_are_free_fermion():
+    """Open XX chain with fields, H = sum_i J_i (X_i X_i+1 + Y_i Y_i+1) + sum_i h_i Z_i,
+    restricted to each fixed-N sector of blocks (k, N - k) over a 5|5 split.  With
+    n_i the bit of qubit i, Z_i = 1 - 2 n_i and the bond term hops a particle with
+    amplitude 2 J_i, so the N-particle eigenvalues are sum_i h_i plus every sum of N
+    eigenvalues of the tridiagonal matrix (-2 h_i on the diagonal, 2 J_i beside it)."""
+    import itertools
+    n, n_lo = 10, 5
+    rng = np.random.default_rng(22)
+    J, h = rng.normal(size=n - 1), rng.normal(size=n)
+    xs, zs, cs = [], [], []
+    for i in range(n - 1):
+        b = (1 << i) | (1 << (i + 1))
+        xs += [b, b]; zs += [0, b]; cs += [J[i], J[i]]   # X X, Y Y (letter form)
+    for i in range(n):
+        xs.append(0); zs.append(1 << i); cs.append(h[i])
+    c = np.array(cs)
+    R = oracle.build_sum(n, np.array(xs, np.uint64), np.array(zs, np.uint64), None, c, np.zeros_like(c))
+    eps = np.linalg.eigvalsh(np.diag(-2.0 * h) + np.diag(2.0 * J, 1) + np.diag(2.0 * J, -1))
+    for N in range(n + 1):
+        blocks = [(k, N - k) for k in range(N + 1) if k <= n_lo and N - k <= n - n_lo]
+        So = oracle.Sector(n, oracle.BLOCKS, n_lo, blocks)
+        assert So.dim == math.comb(n, N)
+        M = _dense_from_apply(So, R)
+        spec = np.sort([h.sum() + eps[list(S)].sum() for S in itertools.combinations(range(n), N)])
+        assert np.abs(np.sort(np.linalg.eigvalsh(M)) - spec).max() <= 1e-12 * (np.abs(eps).sum() + np.abs(h).sum()), N
