@@ -1,6 +1,6 @@
 """GPU apply / expect / rotate vs the oracle on the same seeded inputs.
 
-Tolerances (spec contract): ||H psi||-relative error <= 1e-12 for the
+Tolerances: ||H psi||-relative error <= 1e-12 for the
 FP64 (complex128) path and <= 1e-5 for the FP32 (complex64) path, the latter
 measured against the oracle run on the complex64-rounded input; energies within
 1e-6 Ha (1e-12 for FP64)."""
